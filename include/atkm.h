@@ -1,0 +1,206 @@
+/*
+ * atkm.h -- C interface of the GB300 PCG-ATKM ground-state solver.
+ *
+ * Computes ground states of the 3D rotating dipolar Gross-Pitaevskii energy
+ * (Tang, Wang, Zhang & Zhang, "An efficient and accurate numerical method for
+ * computing the ground states of three-dimensional rotating dipolar
+ * Bose-Einstein condensates under strongly anisotropic trap"):
+ *   - the dipolar potential by the anisotropic truncated kernel method (ATKM,
+ *     §2.2, Eqs. (iden_b2)-(FUk) with the Coulomb reformulation (DDI2Cou3D)),
+ *   - the Fourier-spectral Hamiltonian (§2.1 Eq. (Laplacian), §2.3),
+ *   - the preconditioner, the Riemannian PCG step and its step control
+ *     (§2.3, Algorithm 1).
+ *
+ * Conventions shared by every call
+ *   - Box prod_a [-L_a, L_a]; grid N_a points per axis, N_a even, each N_a a
+ *     product of 2, 3 and 5 only, 2 <= N_a <= 1024; h_a = 2 L_a / N_a; grid
+ *     point j of axis a sits at -L_a + j h_a (§2.1).
+ *   - Arrays are row-major [N_z][N_y][N_x] (x fastest).  Complex arrays are
+ *     interleaved (re, im) pairs, i.e. 2*N_x*N_y*N_z doubles (or floats).
+ *   - Every array argument is a DEVICE pointer owned by the caller, sized for
+ *     the plan's grid, 16-byte aligned (any cudaMalloc / torch allocation is).
+ *     Host pointers are only the small parameter/result structs.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous unless the call says otherwise.
+ *   - Every call returns an atkm_status; none raises, traps or sets errno.
+ *     After a failure atkm_last_error_string(plan) describes it.
+ *   - A plan may be used by one host thread at a time; calls on one plan must
+ *     use one stream (the plan's workspace is shared between calls).
+ */
+#ifndef ATKM_H_
+#define ATKM_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum atkm_status {
+  ATKM_OK = 0,
+  ATKM_ERR_ARG = 1,              /* bad pointer, size or parameter value         */
+  ATKM_ERR_UNSUPPORTED_SIZE = 2, /* N_a odd, not {2,3,5}-smooth, or too large     */
+  ATKM_ERR_OOM = 3,              /* device allocation failed                      */
+  ATKM_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed   */
+  ATKM_NOT_CONVERGED = 5,        /* PCG reached max_iter before the stop rule     */
+  ATKM_STAGNATED = 6,            /* three consecutive exhausted halving loops     */
+  ATKM_ERR_NAN = 7,              /* a NaN/Inf appeared in the PCG scalars         */
+  ATKM_ERR_TIMEOUT = 8           /* reserved: a bounded device wait ran out       */
+} atkm_status;
+
+typedef struct atkm_plan atkm_plan;
+
+/* Plan flags (bit set). */
+#define ATKM_PLAN_F64 0u   /* FP64 workspaces (always present)                  */
+#define ATKM_PLAN_F32 1u   /* also allocate complex64 workspaces for the _f32 calls */
+
+/*
+ * atkm_plan_create -- grid, box, dipole axis; precomputes the truncated-kernel
+ * multiplier ("Precompute the coefficients", Algorithm 1; §2.2 remark: once
+ * per domain and mesh).
+ *   N[3]  grid sizes (N_x, N_y, N_z), see conventions.
+ *   L[3]  box half-lengths, each > 0 and finite.
+ *   n[3]  dipole orientation; | |n| - 1 | must be <= 1e-12 (Eq. (DDI-3D)).
+ *   flags ATKM_PLAN_F64 or ATKM_PLAN_F32.
+ * Builds, in FP64 on the device, U0(nu) = int_{D_2L} e^{-i nu.y}/(4 pi|y|) dy on
+ * the nonnegative frequency octant of the twofold-padded grid (Eq. (FUk)),
+ * from which the dipolar multiplier K = -1 + 3 (n.nu)^2 U0 is formed on the
+ * fly.  Synchronises `stream` before returning.  On success *out owns all
+ * device memory of the plan; on failure *out is NULL and nothing is leaked.
+ */
+int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const double n[3],
+                     unsigned flags, void* stream);
+
+/* Frees the plan and its device memory (synchronises the device). NULL-safe. */
+void atkm_plan_destroy(atkm_plan* plan);
+
+/* Message for the last failing call on `plan` (or a global message when plan is NULL). */
+const char* atkm_last_error_string(const atkm_plan* plan);
+
+/* Bytes of device memory held by the plan. */
+unsigned long long atkm_plan_device_bytes(const atkm_plan* plan);
+
+/*
+ * atkm_plan_copy_U0 -- copies the FP64 octant table U0[|k_z|][|k_y|][|k_x|],
+ * |k_a| = 0..N_a, (N_z+1)(N_y+1)(N_x+1) doubles, to the device buffer `dst`
+ * (ATKM precompute, Eq. (FUk)).  Stream-ordered.
+ */
+int atkm_plan_copy_U0(const atkm_plan* plan, double* dst, void* stream);
+
+/*
+ * atkm_plan_copy_multiplier -- writes the full padded dipolar multiplier
+ * K(k) = -1 + 3 (n.nu_k)^2 U0(nu_k) in FFT order, shape [2N_z][2N_y][2N_x]
+ * doubles, to `dst` (Eq. (DDI2Cou3D) in Fourier space).  Stream-ordered.
+ */
+int atkm_plan_copy_multiplier(const atkm_plan* plan, double* dst, void* stream);
+
+/*
+ * dipolar_potential -- Phi = U_dip * rho by ATKM (§2.2: twofold zero padding,
+ * FFT (Eq. (fouriercoeff)), multiply, inverse FFT (Eq. (U_TrunFour)), real
+ * part, crop).  rho, phi: N doubles each (phi may not alias rho).  Phi does
+ * not include the factor lambda.
+ */
+int dipolar_potential(atkm_plan* plan, const double* rho, double* phi, void* stream);
+
+/* Same with rho = |psi|^2 formed on the fly; psi: N complex (2N doubles). */
+int dipolar_potential_from_psi(atkm_plan* plan, const double* psi, double* phi, void* stream);
+
+/* Same with rho = Re(conj(a) b) formed on the fly (the density variation
+ * of Eq. (Energy_Expend)); a, b: N complex each. */
+int dipolar_potential_from_pair(atkm_plan* plan, const double* a, const double* b, double* phi,
+                                void* stream);
+
+/* FP32-arithmetic variant of dipolar_potential_from_psi (plan needs
+ * ATKM_PLAN_F32): same FP64 interface, but the five FFT passes run in FP32
+ * on complex64 workspaces (half the bytes); the multiplier is formed in FP64
+ * and rounded per use.  Relative error ~1e-6 of max|Phi|. */
+int dipolar_potential_from_psi_f32(atkm_plan* plan, const double* psi, double* phi, void* stream);
+
+/* Physical parameters of the energy (Eqs. (DipGPE0), (Vpoten)). */
+typedef struct atkm_params {
+  double gamma[3]; /* trap frequencies gamma_x, gamma_y, gamma_z */
+  double beta;     /* contact interaction strength */
+  double lambda;   /* dipolar interaction strength */
+  double Omega;    /* rotation frequency */
+} atkm_params;
+
+/*
+ * apply_H -- Hf = -1/2 [[Delta]] f + V f + beta |phi|^2 f + lambda Phi f
+ * - Omega [[L_z]] f (§2.3, the operator H_phi of the energy gradient, with
+ * [[.]] the Fourier-spectral operators of Eq. (Laplacian)).
+ *   f    N complex: the vector H_phi acts on (f == phi gives H_phi phi).
+ *   phi  N complex: the state whose density enters beta |phi|^2.
+ *   Phi  N doubles: the dipolar potential of |phi|^2 (from dipolar_potential).
+ *   Hf   N complex output; must not alias f, phi or Phi.
+ */
+int apply_H(atkm_plan* plan, const atkm_params* prm, const double* f, const double* phi,
+            const double* Phi, double* Hf, void* stream);
+
+/* Energy terms of the discrete functional (§2.3) and the virial residual
+ * I = 2E_kin - 2E_pot + 3E_int + 3E_dip (Eq. (vir_iden)). */
+typedef struct atkm_energy {
+  double E, E_kin, E_pot, E_int, E_dip, E_rot, mu, virial, norm2;
+} atkm_energy;
+
+/*
+ * atkm_energy_parts -- evaluates the energy terms and mu = <H_phi phi, phi>
+ * for (phi, Phi).  Synchronises `stream` and writes *out (host struct).
+ */
+int atkm_energy_parts(atkm_plan* plan, const atkm_params* prm, const double* phi,
+                      const double* Phi, atkm_energy* out, void* stream);
+
+/*
+ * apply_preconditioner -- Pr = P_V^{1/2} P_Delta P_V^{1/2} r (§2.3), with
+ * P_Delta = (alpha - [[Delta]]/2)^{-1} and
+ * P_V = (alpha + V + beta |phi|^2 + |lambda| (1 + sign Phi) Phi / 2)^{-1}.
+ *   alpha  the shift (> 0); pcg_ground_state uses
+ *          <-1/2[[Delta]]phi + V phi + beta|phi|^2 phi, phi> + |lambda <Phi phi, phi>|.
+ *   r, phi N complex; Phi N doubles; Pr N complex output (no aliasing).
+ */
+int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, const double* r,
+                         const double* phi, const double* Phi, double* Pr, void* stream);
+
+/* Precision modes of the PCG driver. */
+#define ATKM_PRECISION_F64 0      /* every step in FP64                          */
+#define ATKM_PRECISION_F32_F64 1  /* complex64 FFT/ATKM/H/P until switch_tol, then FP64 */
+
+typedef struct atkm_pcg_opts {
+  double tol_residual;  /* stop when ||H phi - mu phi|| <= tol_residual (e.g. 1e-8)    */
+  double tol_linf;      /* if > 0, also stop when ||phi_{n+1}-phi_n||_inf <= tol_linf  */
+  int max_iter;         /* iteration cap (ATKM_NOT_CONVERGED when reached)            */
+  int max_halvings;     /* halvings of t per iteration before taking the lowest trial */
+  int precision_mode;   /* ATKM_PRECISION_F64 or ATKM_PRECISION_F32_F64               */
+  double switch_tol;    /* residual at which the F32 phase hands over (e.g. 1e-5)     */
+  int log_capacity;     /* entries available in `log` (0 = no log)                    */
+} atkm_pcg_opts;
+
+/* One record per iteration n (values at phi_n; step fields describe n -> n+1). */
+typedef struct atkm_iter_log {
+  int n, halvings, reset_to_sd, accepted, f32_phase, pad_;
+  double E, mu, residual, linf_step, alpha, beta_cg, d1, curvature, t0, t;
+} atkm_iter_log;
+
+typedef struct atkm_result {
+  double E, mu, E_kin, E_pot, E_int, E_dip, E_rot, virial;
+  double residual, linf_step;
+  int iters, halvings, f32_iters, status;
+  atkm_iter_log* log;   /* host array of opts.log_capacity entries (may be NULL) */
+  int log_count;        /* entries written                                       */
+} atkm_result;
+
+/*
+ * pcg_ground_state -- Algorithm 1 (PCG-ATKM) with the step control of §2.3
+ * (i) PSD fallback when <H phi, p> >= 0, (ii) quadratic-model step
+ * (Eq. (opt_step)) or t = 0.3, (iii) halving until the energy decreases.
+ *   psi_inout  N complex: initial guess in, final state out (normalised on entry).
+ *   out        host struct; out->log (host) receives per-iteration records.
+ * Allocates the PCG vectors on first use (kept by the plan).  Synchronises
+ * `stream` several times per iteration (the step decisions run on the host).
+ * Returns ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN or an
+ * argument/CUDA error; out->status holds the same value.
+ */
+int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opts* opts,
+                     double* psi_inout, atkm_result* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATKM_H_ */

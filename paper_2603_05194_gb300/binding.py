@@ -1,0 +1,237 @@
+"""Thin Python binding of libatkm (include/atkm.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library; this module converts torch
+tensors to device pointers, fills the C structs and checks return codes.  It
+raises if the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libatkm.so")
+
+ATKM_OK = 0
+ATKM_ERR_ARG = 1
+ATKM_ERR_UNSUPPORTED_SIZE = 2
+ATKM_ERR_OOM = 3
+ATKM_ERR_CUDA = 4
+ATKM_NOT_CONVERGED = 5
+ATKM_STAGNATED = 6
+ATKM_ERR_NAN = 7
+ATKM_ERR_TIMEOUT = 8
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED_SIZE", 3: "ERR_OOM", 4: "ERR_CUDA",
+                5: "NOT_CONVERGED", 6: "STAGNATED", 7: "ERR_NAN", 8: "ERR_TIMEOUT"}
+ATKM_PLAN_F32 = 1
+PRECISION_F64 = 0
+PRECISION_F32_F64 = 1
+
+
+class AtkmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double * 3), ("beta", C.c_double), ("lam", C.c_double), ("Omega", C.c_double)]
+
+
+class Energy(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("E", "E_kin", "E_pot", "E_int", "E_dip", "E_rot", "mu", "virial", "norm2")]
+
+
+class PcgOpts(C.Structure):
+    _fields_ = [("tol_residual", C.c_double), ("tol_linf", C.c_double), ("max_iter", C.c_int),
+                ("max_halvings", C.c_int), ("precision_mode", C.c_int), ("switch_tol", C.c_double),
+                ("log_capacity", C.c_int)]
+
+
+class IterLog(C.Structure):
+    _fields_ = [("n", C.c_int), ("halvings", C.c_int), ("reset_to_sd", C.c_int), ("accepted", C.c_int),
+                ("f32_phase", C.c_int), ("pad_", C.c_int)] + \
+               [(k, C.c_double) for k in ("E", "mu", "residual", "linf_step", "alpha", "beta_cg", "d1",
+                                          "curvature", "t0", "t")]
+
+
+class Result(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("E", "mu", "E_kin", "E_pot", "E_int", "E_dip", "E_rot", "virial",
+                                          "residual", "linf_step")] + \
+               [("iters", C.c_int), ("halvings", C.c_int), ("f32_iters", C.c_int), ("status", C.c_int),
+                ("log", C.POINTER(IterLog)), ("log_count", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libatkm.so (built by paper_2603_05194_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libatkm.so not found at {path}: run `python -m paper_2603_05194_gb300.build`")
+    lib = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    sig = {
+        "atkm_plan_create": (ip, [C.POINTER(vp), C.POINTER(C.c_int), dp, dp, C.c_uint, vp]),
+        "atkm_plan_destroy": (None, [vp]),
+        "atkm_last_error_string": (C.c_char_p, [vp]),
+        "atkm_plan_device_bytes": (C.c_ulonglong, [vp]),
+        "atkm_plan_copy_U0": (ip, [vp, vp, vp]),
+        "atkm_plan_copy_multiplier": (ip, [vp, vp, vp]),
+        "dipolar_potential": (ip, [vp, vp, vp, vp]),
+        "dipolar_potential_from_psi": (ip, [vp, vp, vp, vp]),
+        "dipolar_potential_from_pair": (ip, [vp, vp, vp, vp, vp]),
+        "dipolar_potential_from_psi_f32": (ip, [vp, vp, vp, vp]),
+        "apply_H": (ip, [vp, C.POINTER(Params), vp, vp, vp, vp, vp]),
+        "atkm_energy_parts": (ip, [vp, C.POINTER(Params), vp, vp, C.POINTER(Energy), vp]),
+        "apply_preconditioner": (ip, [vp, C.POINTER(Params), C.c_double, vp, vp, vp, vp, vp]),
+        "pcg_ground_state": (ip, [vp, C.POINTER(Params), C.POINTER(PcgOpts), vp, C.POINTER(Result), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_params(gamma, beta, lam, Omega) -> Params:
+    p = Params()
+    p.gamma[:] = [float(g) for g in gamma]
+    p.beta, p.lam, p.Omega = float(beta), float(lam), float(Omega)
+    return p
+
+
+class Plan:
+    """Owning handle of an atkm_plan (grid, box, dipole axis, multiplier)."""
+
+    def __init__(self, N, L, n, f32: bool = False, stream=None):
+        lib = load_library()
+        self.N = tuple(int(v) for v in N)
+        self.L = tuple(float(v) for v in L)
+        self.n = tuple(float(v) for v in n)
+        self.shape = (self.N[2], self.N[1], self.N[0])
+        self._h = C.c_void_p()
+        Na = (C.c_int * 3)(*self.N)
+        La = (C.c_double * 3)(*self.L)
+        na = (C.c_double * 3)(*self.n)
+        code = lib.atkm_plan_create(C.byref(self._h), Na, La, na, ATKM_PLAN_F32 if f32 else 0, _stream(stream))
+        if code != ATKM_OK:
+            raise AtkmError(code, lib.atkm_last_error_string(None).decode())
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.atkm_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code):
+        if code != ATKM_OK:
+            raise AtkmError(code, self._lib.atkm_last_error_string(self._h).decode())
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self._lib.atkm_plan_device_bytes(self._h))
+
+    # ---- multiplier
+    def U0(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.N[2] + 1, self.N[1] + 1, self.N[0] + 1), dtype=torch.float64, device="cuda")
+        self._check(self._lib.atkm_plan_copy_U0(self._h, C.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def multiplier(self, stream=None) -> torch.Tensor:
+        out = torch.empty((2 * self.N[2], 2 * self.N[1], 2 * self.N[0]), dtype=torch.float64, device="cuda")
+        self._check(self._lib.atkm_plan_copy_multiplier(self._h, C.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    # ---- dipolar potential
+    def dipolar_potential(self, rho, out=None, stream=None):
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self._lib.dipolar_potential(self._h, _ptr(rho, torch.float64, self.shape, "rho"),
+                                                _ptr(out, torch.float64, self.shape, "phi"), _stream(stream)))
+        return out
+
+    def dipolar_potential_from_psi(self, psi, out=None, stream=None, f32=False):
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda") if out is None else out
+        fn = self._lib.dipolar_potential_from_psi_f32 if f32 else self._lib.dipolar_potential_from_psi
+        self._check(fn(self._h, _ptr(psi, torch.complex128, self.shape, "psi"),
+                       _ptr(out, torch.float64, self.shape, "phi"), _stream(stream)))
+        return out
+
+    def dipolar_potential_from_pair(self, a, b, out=None, stream=None):
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self._lib.dipolar_potential_from_pair(
+            self._h, _ptr(a, torch.complex128, self.shape, "a"), _ptr(b, torch.complex128, self.shape, "b"),
+            _ptr(out, torch.float64, self.shape, "phi"), _stream(stream)))
+        return out
+
+    # ---- Hamiltonian, energy, preconditioner
+    def apply_H(self, prm: Params, f, phi, Phi, out=None, stream=None):
+        out = torch.empty(self.shape, dtype=torch.complex128, device="cuda") if out is None else out
+        self._check(self._lib.apply_H(self._h, C.byref(prm), _ptr(f, torch.complex128, self.shape, "f"),
+                                      _ptr(phi, torch.complex128, self.shape, "phi"),
+                                      _ptr(Phi, torch.float64, self.shape, "Phi"),
+                                      _ptr(out, torch.complex128, self.shape, "Hf"), _stream(stream)))
+        return out
+
+    def energy_parts(self, prm: Params, phi, Phi, stream=None) -> dict:
+        e = Energy()
+        self._check(self._lib.atkm_energy_parts(self._h, C.byref(prm), _ptr(phi, torch.complex128, self.shape, "phi"),
+                                                _ptr(Phi, torch.float64, self.shape, "Phi"), C.byref(e),
+                                                _stream(stream)))
+        return {k: getattr(e, k) for k, _ in Energy._fields_}
+
+    def apply_preconditioner(self, prm: Params, alpha: float, r, phi, Phi, out=None, stream=None):
+        out = torch.empty(self.shape, dtype=torch.complex128, device="cuda") if out is None else out
+        self._check(self._lib.apply_preconditioner(
+            self._h, C.byref(prm), C.c_double(alpha), _ptr(r, torch.complex128, self.shape, "r"),
+            _ptr(phi, torch.complex128, self.shape, "phi"), _ptr(Phi, torch.float64, self.shape, "Phi"),
+            _ptr(out, torch.complex128, self.shape, "Pr"), _stream(stream)))
+        return out
+
+    # ---- Algorithm 1
+    def pcg_ground_state(self, prm: Params, psi, tol_residual=1e-8, tol_linf=0.0, max_iter=10000,
+                         max_halvings=20, precision=PRECISION_F64, switch_tol=1e-5, log_capacity=0,
+                         stream=None, check=True) -> dict:
+        opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, log_capacity)
+        res = Result()
+        logs = (IterLog * max(1, log_capacity))()
+        res.log = C.cast(logs, C.POINTER(IterLog)) if log_capacity > 0 else C.POINTER(IterLog)()
+        code = self._lib.pcg_ground_state(self._h, C.byref(prm), C.byref(opts),
+                                          _ptr(psi, torch.complex128, self.shape, "psi"), C.byref(res),
+                                          _stream(stream))
+        if check and code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED):
+            self._check(code)
+        out = {k: getattr(res, k) for k, _ in Result._fields_ if k != "log"}
+        out["status_name"] = STATUS_NAMES.get(res.status, str(res.status))
+        out["log"] = [{k: getattr(logs[i], k) for k, _ in IterLog._fields_ if k != "pad_"}
+                      for i in range(res.log_count)]
+        return out

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle on the
+same seeded inputs.  Tolerances follow the arithmetic of each row:
+  * U0 / K (FP64 precompute, two independent quadratures): 1e-12 relative to
+    max|U0| (absolute in K, which is O(1));
+  * Phi (FP64 FFT convolution): ||dPhi||_2 / ||Phi||_2 <= 1e-11;
+  * H f, P r (FP64 spectral operators): relative 2-norm <= 1e-12;
+  * energies and mu: relative <= 1e-10 (full PCG runs), 1e-12 for a fixed state.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import atkm_workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+SMALL_CASES = [
+    # (N, L, n): several tiles, ragged tails, radix 2/3/5 mixes, tilted axes
+    ((32, 32, 16), (8.0, 8.0, 2.0), (0.0, 0.0, 1.0)),
+    ((24, 20, 12), (5.0, 4.0, 1.2), (0.6, 0.0, 0.8)),
+    ((40, 36, 10), (6.0, 5.5, 1.0), (0.5, 0.5, math.sqrt(0.5))),
+    ((6, 4, 2), (1.0, 0.8, 0.5), (1.0, 0.0, 0.0)),
+    ((96, 80, 18), (10.0, 9.0, 1.5), (0.0, 0.6, 0.8)),
+]
+
+
+@pytest.mark.parametrize("N,L,n", SMALL_CASES)
+def test_U0_and_multiplier_match_oracle(lib, N, L, n):
+    plan = lib.Plan(N, L, n)
+    U0 = host(plan.U0())
+    ref = O.truncated_coulomb_fourier(N, L)
+    assert np.max(np.abs(U0 - ref)) <= 1e-12 * np.max(np.abs(ref))
+    K = host(plan.multiplier())
+    Kref = O.dipolar_multiplier(N, L, n, ref)
+    assert np.max(np.abs(K - Kref)) <= 1e-11
+
+
+@pytest.mark.parametrize("N,L,n", SMALL_CASES)
+def test_dipolar_potential_parity(lib, N, L, n):
+    plan = lib.Plan(N, L, n)
+    oplan = O.Plan(N, L, n)
+    shape = (N[2], N[1], N[0])
+    # smooth density and a white-noise density (stresses every frequency)
+    rho_s = np.abs(W.random_smooth_field(N, L, (1.0, 1.1, 5.0), seed=101)) ** 2
+    rho_w = W.random_field(shape, 102, complex_valued=False)
+    for rho in (rho_s, rho_w):
+        got = host(plan.dipolar_potential(dev(rho)))
+        ref = oplan.dipolar_potential(rho)
+        assert rel2(got, ref) <= 1e-11
+    psi = W.random_smooth_field(N, L, (1.0, 1.1, 5.0), seed=103)
+    got = host(plan.dipolar_potential_from_psi(dev(psi)))
+    assert rel2(got, oplan.dipolar_potential(np.abs(psi) ** 2)) <= 1e-11
+    a = W.random_field(shape, 104)
+    b = W.random_field(shape, 105)
+    got = host(plan.dipolar_potential_from_pair(dev(a), dev(b)))
+    assert rel2(got, oplan.dipolar_potential(np.real(np.conj(a) * b))) <= 1e-11
+
+
+def test_dipolar_potential_gaussian_closed_form(lib):
+    """Standalone check of the 32x32x16 workload family: isotropic sigma=1
+    Gaussian on [-8,8]^3 at 64^3 against the exact dipolar potential."""
+    from tests.test_oracle_kernel import iso_gaussian_dipolar
+    N, L = (64, 64, 64), (8.0, 8.0, 8.0)
+    n = (0.0, 0.0, 1.0)
+    rho, _, Phi = iso_gaussian_dipolar(N, L, n)
+    plan = lib.Plan(N, L, n)
+    got = host(plan.dipolar_potential(dev(rho)))
+    assert np.max(np.abs(got - Phi)) <= 1e-12 * np.max(np.abs(Phi))
+
+
+def _state(N, L, gamma, seed):
+    phi = W.random_smooth_field(N, L, gamma, seed=seed)
+    h3 = np.prod([2 * L[i] / N[i] for i in range(3)])
+    return phi / math.sqrt(h3 * np.sum(np.abs(phi) ** 2))
+
+
+@pytest.mark.parametrize("N,L,n", SMALL_CASES)
+def test_apply_H_energy_and_preconditioner_parity(lib, N, L, n):
+    gamma, beta, lam, Om = (1.0, 1.3, 6.0), 40.0, -12.0, 0.55
+    plan = lib.Plan(N, L, n)
+    oplan = O.Plan(N, L, n)
+    oprm = O.Params(gamma, beta, lam, Om)
+    prm = lib.make_params(gamma, beta, lam, Om)
+    phi = _state(N, L, gamma, 201)
+    f = W.random_field(oplan.grid.shape, 202)
+    Phi = oplan.dipolar_potential(np.abs(phi) ** 2)
+    Hf = host(plan.apply_H(prm, dev(f), dev(phi), dev(Phi)))
+    assert rel2(Hf, O.apply_H(oplan, oprm, f, phi, Phi)) <= 1e-12
+    e = plan.energy_parts(prm, dev(phi), dev(Phi))
+    p = O.energy_parts(oplan, oprm, phi, Phi)
+    scale = abs(p["E"]) + abs(p["E_kin"]) + abs(p["E_pot"])
+    for k in ("E", "E_kin", "E_pot", "E_int", "E_dip", "E_rot", "virial"):
+        assert abs(e[k] - p[k]) <= 1e-12 * scale, k
+    mu = O.inner(O.apply_H(oplan, oprm, phi, phi, Phi), phi, oplan.grid)
+    assert abs(e["mu"] - mu) <= 1e-12 * abs(mu)
+    alpha = O.precond_shift(oplan, oprm, phi, Phi)
+    Pr = host(plan.apply_preconditioner(prm, alpha, dev(f), dev(phi), dev(Phi)))
+    assert rel2(Pr, O.apply_precond(oplan, oprm, f, phi, Phi, alpha)) <= 1e-12
+
+
+def _run_pair(lib, w, max_iter, tol=1e-8, precision=0):
+    plan = lib.Plan(w.N, w.L, w.n, f32=(precision != 0))
+    prm = lib.make_params(w.gamma, w.beta, w.lam, w.Omega)
+    psi = dev(W.initial_guess(w))
+    res = plan.pcg_ground_state(prm, psi, tol_residual=tol, max_iter=max_iter, log_capacity=max_iter + 2,
+                                precision=precision)
+    return plan, psi, res
+
+
+@pytest.fixture(scope="module")
+def cfg1_oracle():
+    w = W.CONFIGS["cfg1_32x32x16"]
+    oplan = O.Plan(w.N, w.L, w.n)
+    oprm = O.Params(w.gamma, w.beta, w.lam, w.Omega)
+    return w, O.pcg_ground_state(oplan, oprm, W.initial_guess(w), O.PcgOptions(max_iter=400))
+
+
+def test_pcg_cfg1_full_run_parity(lib, cfg1_oracle):
+    w, ref = cfg1_oracle
+    plan, psi, res = _run_pair(lib, w, 400)
+    assert res["status"] == 0 and ref.status == O.OK
+    assert res["residual"] <= 1e-8
+    assert abs(res["E"] - ref.parts["E"]) <= 1e-10 * abs(ref.parts["E"])
+    assert abs(res["mu"] - ref.mu) <= 1e-10 * abs(ref.mu)
+    # trajectory: energies agree while they are well above roundoff
+    for a, b in zip(res["log"][:20], ref.log[:20]):
+        assert abs(a["E"] - b["E"]) <= 1e-10 * abs(b["E"])
+    # final states agree up to a global phase
+    phi = host(psi)
+    kappa = np.vdot(ref.phi, phi) / np.vdot(ref.phi, ref.phi)
+    assert np.linalg.norm(phi - kappa * ref.phi) / np.linalg.norm(ref.phi) <= 1e-6
+
+
+def test_pcg_cfg2_first_iterations_parity(lib):
+    w = W.CONFIGS["cfg2_128x128x32"]
+    oplan = O.Plan(w.N, w.L, w.n)
+    oprm = O.Params(w.gamma, w.beta, w.lam, w.Omega)
+    k = 4
+    ref = O.pcg_ground_state(oplan, oprm, W.initial_guess(w), O.PcgOptions(max_iter=k))
+    plan, psi, res = _run_pair(lib, w, k)
+    assert res["iters"] == k
+    for a, b in zip(res["log"], ref.log):
+        assert abs(a["E"] - b["E"]) <= 1e-10 * abs(b["E"])
+        assert abs(a["residual"] - b["residual"]) <= 1e-8 * b["residual"]
+        assert a["halvings"] == b.get("halvings", a["halvings"])
+    phi = host(psi)
+    assert rel2(phi, ref.phi) <= 1e-9
+
+
+def test_pcg_harmonic_oscillator(lib):
+    N, L = (32, 32, 32), (8.0, 8.0, 4.0)
+    plan = lib.Plan(N, L, (0, 0, 1))
+    prm = lib.make_params((1.0, 1.0, 4.0), 0.0, 0.0, 0.0)
+    psi = dev(W.random_smooth_field(N, L, (0.8, 0.9, 3.0), seed=7))
+    res = plan.pcg_ground_state(prm, psi, tol_residual=1e-10, max_iter=500)
+    assert res["status"] == 0
+    assert abs(res["E"] - 3.0) < 1e-10 and abs(res["mu"] - 3.0) < 1e-10
+
+
+def test_pcg_invariants_along_run(lib):
+    w = W.CONFIGS["cfg1_32x32x16"]
+    plan, psi, res = _run_pair(lib, w, 400)
+    Es = [e["E"] for e in res["log"]]
+    for a, b in zip(Es, Es[1:]):
+        assert b <= a + 32 * np.finfo(float).eps * abs(a)
+    # mu - E identity and unit norm of the final state
+    assert abs(res["mu"] - (res["E"] + res["E_int"] + res["E_dip"])) <= 1e-12 * abs(res["mu"])
+    h3 = np.prod([2 * w.L[i] / w.N[i] for i in range(3)])
+    assert abs(h3 * float(torch.sum(torch.abs(psi) ** 2)) - 1.0) < 1e-13
+
+
+def test_mixed_precision_reaches_fp64_energy(lib):
+    w = W.CONFIGS["cfg1_32x32x16"]
+    _, _, r64 = _run_pair(lib, w, 400)
+    _, _, rmx = _run_pair(lib, w, 400, precision=1)
+    assert rmx["status"] == 0 and rmx["residual"] <= 1e-8
+    assert rmx["f32_iters"] > 0
+    assert abs(rmx["E"] - r64["E"]) <= 1e-9 * abs(r64["E"])
+
+
+def test_f32_atkm_close_to_oracle(lib):
+    N, L, n = (32, 32, 16), (8.0, 8.0, 2.0), (0.6, 0.0, 0.8)
+    plan = lib.Plan(N, L, n, f32=True)
+    psi = W.random_smooth_field(N, L, (1.0, 1.1, 5.0), seed=301)
+    got = host(plan.dipolar_potential_from_psi(dev(psi), f32=True))
+    ref = O.Plan(N, L, n).dipolar_potential(np.abs(psi) ** 2)
+    assert rel2(got, ref) <= 2e-6
+
+
+@pytest.mark.parametrize("N,L,n,code", [
+    ((31, 32, 16), (8, 8, 2), (0, 0, 1), 2),      # odd
+    ((28, 32, 16), (8, 8, 2), (0, 0, 1), 2),      # factor 7
+    ((32, 32, 16), (8, 8, 2), (0, 0, 1.001), 1),  # |n| != 1
+    ((32, 32, 16), (8, -8, 2), (0, 0, 1), 1),     # negative box
+    ((2048, 32, 16), (8, 8, 2), (0, 0, 1), 2),    # beyond the line limit
+])
+def test_plan_rejects_bad_arguments(lib, N, L, n, code):
+    with pytest.raises(lib.AtkmError) as ei:
+        lib.Plan(N, L, n)
+    assert ei.value.code == code
+
+
+def test_smallest_grid_and_degenerate_inputs(lib):
+    N, L, n = (2, 2, 2), (1.0, 1.0, 1.0), (0, 0, 1)
+    plan = lib.Plan(N, L, n)
+    oplan = O.Plan(N, L, n)
+    rho = W.random_field((2, 2, 2), 401, complex_valued=False)
+    assert rel2(host(plan.dipolar_potential(dev(rho))), oplan.dipolar_potential(rho)) <= 1e-11
+    # zero density gives a zero potential; a zero initial state is rejected
+    z = torch.zeros((2, 2, 2), dtype=torch.float64, device="cuda")
+    assert float(plan.dipolar_potential(z).abs().max()) == 0.0
+    prm = lib.make_params((1, 1, 1), 0, 0, 0)
+    psi0 = torch.zeros((2, 2, 2), dtype=torch.complex128, device="cuda")
+    res = plan.pcg_ground_state(prm, psi0, check=False)
+    assert res["status"] == 7
+
+
+@pytest.mark.slow
+def test_cfg3_dipolar_potential_full_size(lib):
+    """256x256x64 (the bench grid): full ATKM against the oracle, FP64 and FP32."""
+    w = W.CONFIGS["cfg3_256x256x64"]
+    plan = lib.Plan(w.N, w.L, w.n, f32=True)
+    psi = W.initial_guess(w)
+    ref = O.Plan(w.N, w.L, w.n).dipolar_potential(np.abs(psi) ** 2)
+    got = host(plan.dipolar_potential_from_psi(dev(psi)))
+    assert rel2(got, ref) <= 1e-11
+    got32 = host(plan.dipolar_potential_from_psi(dev(psi), f32=True))
+    assert rel2(got32, ref) <= 2e-6
