@@ -79,6 +79,34 @@ const char* atkm_last_error_string(const atkm_plan* plan);
 unsigned long long atkm_plan_device_bytes(const atkm_plan* plan);
 
 /*
+ * Per-kernel timing (opt-in).  While profiling is on, every pass kernel of the
+ * spectral operators is bracketed by CUDA events recorded on the stream it is
+ * launched on, and tagged with the algorithmic HBM bytes and flops of that
+ * launch (bytes: each input read once and each output written once; flops:
+ * 5 n log2 n per complex FFT of length n).  Library extension for
+ * measurement; the paper has no counterpart.
+ */
+typedef struct atkm_kernel_stat {
+  char name[32];            /* pass name, e.g. "atkm_z_f32"                 */
+  int launches;             /* launches recorded since profiling was enabled */
+  int pad_;
+  double ms_total;          /* summed CUDA-event time of those launches      */
+  double bytes_total;       /* summed algorithmic bytes                      */
+  double flops_total;       /* summed algorithmic flops                      */
+} atkm_kernel_stat;
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * plans, all calls); the difference around a region counts its launches. */
+unsigned long long atkm_launch_count(void);
+
+/* on != 0 clears the record and starts recording; on == 0 stops. */
+int atkm_plan_set_profiling(atkm_plan* plan, int on);
+
+/* Synchronises the device, aggregates the record per pass name into
+ * out[0..capacity) and writes the number of distinct passes to *count. */
+int atkm_plan_kernel_stats(atkm_plan* plan, atkm_kernel_stat* out, int capacity, int* count);
+
+/*
  * atkm_plan_copy_U0 -- copies the FP64 octant table U0[|k_z|][|k_y|][|k_x|],
  * |k_a| = 0..N_a, (N_z+1)(N_y+1)(N_x+1) doubles, to the device buffer `dst`
  * (ATKM precompute, Eq. (FUk)).  Stream-ordered.
@@ -170,6 +198,10 @@ typedef struct atkm_pcg_opts {
   int precision_mode;   /* ATKM_PRECISION_F64 or ATKM_PRECISION_F32_F64               */
   double switch_tol;    /* residual at which the F32 phase hands over (e.g. 1e-5)     */
   int log_capacity;     /* entries available in `log` (0 = no log)                    */
+  int resume;           /* != 0: continue the solve this plan ran last (psi_inout is
+                           then output only); the iteration count, direction memory,
+                           precision phase and energy carry over; max_iter counts
+                           the iterations of this call                              */
 } atkm_pcg_opts;
 
 /* One record per iteration n (values at phi_n; step fields describe n -> n+1). */

@@ -47,7 +47,7 @@ class Energy(C.Structure):
 class PcgOpts(C.Structure):
     _fields_ = [("tol_residual", C.c_double), ("tol_linf", C.c_double), ("max_iter", C.c_int),
                 ("max_halvings", C.c_int), ("precision_mode", C.c_int), ("switch_tol", C.c_double),
-                ("log_capacity", C.c_int)]
+                ("log_capacity", C.c_int), ("resume", C.c_int)]
 
 
 class IterLog(C.Structure):
@@ -55,6 +55,11 @@ class IterLog(C.Structure):
                 ("f32_phase", C.c_int), ("pad_", C.c_int)] + \
                [(k, C.c_double) for k in ("E", "mu", "residual", "linf_step", "alpha", "beta_cg", "d1",
                                           "curvature", "t0", "t")]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int), ("pad_", C.c_int), ("ms_total", C.c_double),
+                ("bytes_total", C.c_double), ("flops_total", C.c_double)]
 
 
 class Result(C.Structure):
@@ -91,6 +96,9 @@ def load_library(path: str = LIB_PATH):
         "atkm_energy_parts": (ip, [vp, C.POINTER(Params), vp, vp, C.POINTER(Energy), vp]),
         "apply_preconditioner": (ip, [vp, C.POINTER(Params), C.c_double, vp, vp, vp, vp, vp]),
         "pcg_ground_state": (ip, [vp, C.POINTER(Params), C.POINTER(PcgOpts), vp, C.POINTER(Result), vp]),
+        "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
+        "atkm_launch_count": (C.c_ulonglong, []),
+        "atkm_plan_kernel_stats": (ip, [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -98,6 +106,11 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libatkm in this process so far."""
+    return int(load_library().atkm_launch_count())
 
 
 def _ptr(t: torch.Tensor, dtype, shape, name):
@@ -161,6 +174,19 @@ class Plan:
     def device_bytes(self) -> int:
         return int(self._lib.atkm_plan_device_bytes(self._h))
 
+    # ---- measurement support
+    def set_profiling(self, on: bool):
+        self._check(self._lib.atkm_plan_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self) -> list:
+        cap = 64
+        arr = (KernelStat * cap)()
+        cnt = C.c_int(0)
+        self._check(self._lib.atkm_plan_kernel_stats(self._h, arr, cap, C.byref(cnt)))
+        return [dict(name=arr[i].name.decode(), launches=arr[i].launches, ms_total=arr[i].ms_total,
+                     bytes_total=arr[i].bytes_total, flops_total=arr[i].flops_total)
+                for i in range(min(cnt.value, cap))]
+
     # ---- multiplier
     def U0(self, stream=None) -> torch.Tensor:
         out = torch.empty((self.N[2] + 1, self.N[1] + 1, self.N[0] + 1), dtype=torch.float64, device="cuda")
@@ -220,8 +246,9 @@ class Plan:
     # ---- Algorithm 1
     def pcg_ground_state(self, prm: Params, psi, tol_residual=1e-8, tol_linf=0.0, max_iter=10000,
                          max_halvings=20, precision=PRECISION_F64, switch_tol=1e-5, log_capacity=0,
-                         stream=None, check=True) -> dict:
-        opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, log_capacity)
+                         stream=None, check=True, resume=False) -> dict:
+        opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, log_capacity,
+                       1 if resume else 0)
         res = Result()
         logs = (IterLog * max(1, log_capacity))()
         res.log = C.cast(logs, C.POINTER(IterLog)) if log_capacity > 0 else C.POINTER(IterLog)()

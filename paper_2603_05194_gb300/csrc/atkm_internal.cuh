@@ -63,9 +63,10 @@ struct FftLen {
   const float2* tw32;
 };
 
-template <typename R> __device__ __forceinline__ const cx<R>* tw_table(const FftLen& f);
-template <> __device__ __forceinline__ const double2* tw_table<double>(const FftLen& f) { return f.tw64; }
-template <> __device__ __forceinline__ const float2* tw_table<float>(const FftLen& f) { return f.tw32; }
+template <typename R> __host__ __device__ __forceinline__ const cx<R>* tw_table(const FftLen& f);
+template <> __host__ __device__ __forceinline__ const double2* tw_table<double>(const FftLen& f) { return f.tw64; }
+template <> __host__ __device__ __forceinline__ const float2* tw_table<float>(const FftLen& f) { return f.tw32; }
+template <typename R> inline const cx<R>* tw_table_host(const FftLen& f) { return tw_table<R>(f); }
 
 // Exact trigonometric constants of the small DFTs (closed forms in radicals).
 #define ATKM_SQRT1_2 0.70710678118654752440084436210485
@@ -240,6 +241,7 @@ struct Phys {  // physical parameters passed by value to kernels
 };
 
 struct PcgBuffers;  // defined in pcg.cu
+struct Profiler;    // defined in plan.cu
 
 }  // namespace atkm
 
@@ -260,6 +262,7 @@ struct atkm_plan {
   double2* tw64;       // twiddle pool
   float2* tw32;
   double* U0;          // octant (Nz+1)(Ny+1)(Nx+1)
+  float* U0f;          // FP32 copy of U0 (FP32 workspaces only)
   double2* W1;         // [Nz][Ny][Mx]
   double2* W2;         // [Nz][My][Mx]
   double2* T1;         // [Nz][Ny][Nx]
@@ -271,6 +274,8 @@ struct atkm_plan {
   double* scal;        // device scalars
   double* scal_host;   // pinned mirror
   atkm::PcgBuffers* pcg;
+  atkm::Profiler* prof;  // non-null while profiling is on
+  atkm::Profiler* prof_stopped_;  // last record after profiling was switched off
   unsigned long long bytes;
   std::string err;
 };
@@ -282,6 +287,13 @@ extern thread_local std::string g_last_error;
 int fail(atkm_plan* p, int code, const std::string& msg);
 int cuda_fail(atkm_plan* p, cudaError_t e, const char* where);
 cudaError_t dev_alloc(atkm_plan* p, void** ptr, size_t bytes);
+
+// Process-wide count of kernel launches issued by the library.
+void count_launches(int n);
+
+// Profiling hooks: no-ops unless profiling is on.  `name` must be a literal.
+void prof_begin(atkm_plan* p, const char* name, double bytes, double flops, cudaStream_t st);
+void prof_end(atkm_plan* p, cudaStream_t st);
 
 // Launchers (passes.cu).  All enqueue on `st`.
 enum AtkmSrc { SRC_RHO = 0, SRC_PSI = 1, SRC_PAIR = 2 };
@@ -296,7 +308,6 @@ cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double
 template <typename R>
 cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev, const double* r,
                            const double* phi, const double* Phi, double* Pr, cudaStream_t st);
-cudaError_t launch_multiplier_full(const atkm_plan* p, double* dst, cudaStream_t st);
 
 // Reductions (pcg.cu)
 cudaError_t launch_finalize(atkm_plan* p, int nslots, int nblocks, int dst_slot, cudaStream_t st);

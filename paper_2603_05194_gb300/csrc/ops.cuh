@@ -1,0 +1,521 @@
+// Pass layer of the spectral operators: each axis pass of ATKM, H_phi f and
+// the preconditioner is an "op" (load / spectral multiply / store, with fused
+// reductions) run by one of two line-FFT engines:
+//   * FastFft: power-of-two lengths 16..1024 known at compile time; each
+//     thread keeps 8 elements of one line in registers, radix-8 Stockham
+//     stages (plus one radix-2/4 stage) exchange through padded, double-
+//     buffered shared memory with one barrier per stage, and the spectral
+//     multiply runs on the registers between forward and inverse transforms;
+//   * the generic shared-memory engine of atkm_internal.cuh for the other
+//     {2,3,5}-smooth lengths.
+// A line is addressed by (o, x): line-major (x-axis) passes use o = line
+// index (z N_y + y); strided passes use o = the outer index (blockIdx.y) and
+// x = the column, T adjacent columns per CTA so global accesses coalesce.
+#pragma once
+
+#include <math.h>
+
+#include "atkm_internal.cuh"
+
+namespace atkm {
+
+// ------------------------------------------------------------ constants
+template <typename R> struct Cst {
+  int Nx, Ny, Nz, Mx, My, Mz;
+  R kx, ky, kz;     // pi / L_a: nu of an unpadded frequency index
+  R pkx, pky, pkz;  // pi / (2 L_a): nu of a padded frequency index
+  R Lx, Ly, Lz, hx, hy, hz;
+};
+
+template <typename R> inline Cst<R> make_cst(const Geo& g) {
+  const double pi = 3.14159265358979323846264338327950288;
+  Cst<R> c;
+  c.Nx = g.Nx; c.Ny = g.Ny; c.Nz = g.Nz; c.Mx = g.Mx; c.My = g.My; c.Mz = g.Mz;
+  c.kx = (R)(pi / g.Lx); c.ky = (R)(pi / g.Ly); c.kz = (R)(pi / g.Lz);
+  c.pkx = (R)(pi / (2.0 * g.Lx)); c.pky = (R)(pi / (2.0 * g.Ly)); c.pkz = (R)(pi / (2.0 * g.Lz));
+  c.Lx = (R)g.Lx; c.Ly = (R)g.Ly; c.Lz = (R)g.Lz; c.hx = (R)g.hx; c.hy = (R)g.hy; c.hz = (R)g.hz;
+  return c;
+}
+
+template <typename R> struct PhysR {
+  R gx2, gy2, gz2, beta, lambda, Omega;
+};
+template <typename R> inline PhysR<R> make_physr(const Phys& p) {
+  PhysR<R> q;
+  q.gx2 = (R)p.gx2; q.gy2 = (R)p.gy2; q.gz2 = (R)p.gz2;
+  q.beta = (R)p.beta; q.lambda = (R)p.lambda; q.Omega = (R)p.Omega;
+  return q;
+}
+
+__device__ __forceinline__ int kfreq(int m, int M) { return m < (M >> 1) ? m : m - M; }
+__device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
+
+template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { return mk<R>((R)z.x, (R)z.y); }
+template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R)0, (R)0); }
+
+template <typename R> __device__ __forceinline__ R rsq(R v);
+template <> __device__ __forceinline__ double rsq<double>(double v) { return rsqrt(v); }
+template <> __device__ __forceinline__ float rsq<float>(float v) { return rsqrtf(v); }
+
+// ------------------------------------------------------------- FastFft
+template <typename R> struct SmemShift;  // one pad element per 128 bytes
+template <> struct SmemShift<double> { static constexpr int value = 3; };
+template <> struct SmemShift<float> { static constexpr int value = 4; };
+
+constexpr int kFastElems = 2048;  // elements per CTA (256 threads x 8)
+
+template <int L> struct FastCfg {
+  static constexpr int TPL = L / 8;             // threads per line
+  static constexpr int T = kFastElems / L;      // lines per CTA
+  static constexpr int A = (L >= 512) ? 3 : (L >= 64 ? 2 : 1);  // radix-8 stages
+  static constexpr int REM = L / (A == 3 ? 512 : (A == 2 ? 64 : 8));  // 1, 2 or 4
+};
+
+template <typename R, int L> struct FastSmem {
+  static constexpr int buf = kFastElems + (kFastElems >> SmemShift<R>::value) + 1;
+  static constexpr size_t bytes = (size_t)(L + 2 * buf) * sizeof(cx<R>);
+};
+
+template <typename R, int L, bool LM> __device__ __forceinline__ int fsa(int t, int pos) {
+  const int lin = LM ? t * L + pos : pos * FastCfg<L>::T + t;
+  return lin + (lin >> SmemShift<R>::value);
+}
+
+// Transforms the 8 register elements v[r] = line[j + TPL r] of line t in place
+// (sign S, unnormalised); on return v[r] holds frequency j + TPL r.
+template <typename R, int L, int S, bool LM>
+__device__ __forceinline__ void fast_fft(cx<R> (&v)[8], cx<R>* b0, cx<R>* b1, const cx<R>* tw, int t, int j) {
+  using C = FastCfg<L>;
+  int Ns = 1;
+#pragma unroll
+  for (int s = 0; s < C::A; ++s) {
+    const int k = j & (Ns - 1);
+    if (s > 0) {
+      const int tws = L / (8 * Ns);
+#pragma unroll
+      for (int r = 1; r < 8; ++r) {
+        const cx<R> w = tw[k * r * tws];
+        v[r] = (S < 0) ? cmul<R>(v[r], w) : cmulc<R>(v[r], w);
+      }
+    }
+    Dft<R, 8, S>::run(v);
+    const bool last = (s == C::A - 1) && (C::REM == 1);
+    if (!last) {
+      cx<R>* b = (s & 1) ? b1 : b0;
+      const int base = (j - k) * 8 + k;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) b[fsa<R, L, LM>(t, base + r * Ns)] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = b[fsa<R, L, LM>(t, j + C::TPL * r)];
+    }
+    Ns *= 8;
+  }
+  if constexpr (C::REM > 1) {
+    constexpr int Q = C::REM, M = 8 / C::REM;  // M butterflies of radix Q per thread
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int b = j + C::TPL * m;  // butterfly index = its twiddle exponent base (Ns = L/Q)
+      cx<R> u[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) u[q] = v[m + M * q];
+#pragma unroll
+      for (int q = 1; q < Q; ++q) {
+        const cx<R> w = tw[b * q];
+        u[q] = (S < 0) ? cmul<R>(u[q], w) : cmulc<R>(u[q], w);
+      }
+      Dft<R, Q, S>::run(u);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[m + M * q] = u[q];
+    }
+  }
+}
+
+// ------------------------------------------------------------ op traits
+template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
+  static constexpr int kSign1 = S1;       // sign of the first transform
+  static constexpr bool kSecond = SECOND;  // inverse transform after the spectral step
+  static constexpr int kRed = NRED;        // fused reduction slots
+  static constexpr bool kLM = LM;          // line-major (x) pass
+  double* part = nullptr;                  // reduction partials [slot][block]
+  int pstride = 0;
+};
+
+// ------------------------------------------------------------ kernels
+template <typename R, int NR>
+__device__ __forceinline__ void reduce_out(R (&acc)[NR], double* part, int pstride) {
+  double d[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s) d[s] = (double)acc[s];
+  block_reduce_store<NR>(d, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+template <typename R, int L, class Op>
+__global__ void __launch_bounds__(kThreads) k_fast(Op op, const cx<R>* __restrict__ twg) {
+  using C = FastCfg<L>;
+  extern __shared__ __align__(16) unsigned char fast_smem[];
+  cx<R>* tw = reinterpret_cast<cx<R>*>(fast_smem);
+  cx<R>* b0 = tw + L;
+  cx<R>* b1 = b0 + FastSmem<R, L>::buf;
+  int t, j;
+  if (Op::kLM) { t = threadIdx.x / C::TPL; j = threadIdx.x % C::TPL; }
+  else { j = threadIdx.x / C::T; t = threadIdx.x % C::T; }
+  const int o = Op::kLM ? blockIdx.x * C::T + t : blockIdx.y;
+  const int x = Op::kLM ? 0 : blockIdx.x * C::T + t;
+  const bool ok = op.valid(o, x);
+  cx<R> v[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = ok ? op.load(o, x, j + C::TPL * r) : czero<R>();
+  for (int i = threadIdx.x; i < L; i += kThreads) tw[i] = twg[i];
+  __syncthreads();
+  constexpr int NR = Op::kRed > 0 ? Op::kRed : 1;
+  R acc[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s) acc[s] = (R)0;
+  fast_fft<R, L, Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
+  if (ok) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) op.spectral(o, x, j + C::TPL * r, v[r], acc);
+  }
+  if (Op::kSecond) {
+    __syncthreads();
+    fast_fft<R, L, -Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
+  }
+  if (ok) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
+  }
+  if (Op::kRed > 0) reduce_out<R, NR>(acc, op.part, op.pstride);
+}
+
+template <typename R, class Op>
+__global__ void __launch_bounds__(kThreads) k_generic(Op op, FftLen f, int T) {
+  extern __shared__ __align__(16) unsigned char gen_smem[];
+  cx<R>* tile = reinterpret_cast<cx<R>*>(gen_smem);
+  cx<R>* tw = tile + T * f.L;
+  const int L = f.L;
+  for (int e = threadIdx.x; e < T * L; e += kThreads) {
+    int t, pos;
+    if (Op::kLM) { t = e / L; pos = e - t * L; } else { pos = e / T; t = e - pos * T; }
+    const int o = Op::kLM ? blockIdx.x * T + t : blockIdx.y;
+    const int x = Op::kLM ? 0 : blockIdx.x * T + t;
+    tile[e] = op.valid(o, x) ? op.load(o, x, pos) : czero<R>();
+  }
+  load_tw<R>(tw, f);
+  __syncthreads();
+  fft_tile<R, Op::kSign1, Op::kLM>(tile, tw, f, T);
+  constexpr int NR = Op::kRed > 0 ? Op::kRed : 1;
+  R acc[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s) acc[s] = (R)0;
+  for (int e = threadIdx.x; e < T * L; e += kThreads) {
+    int t, pos;
+    if (Op::kLM) { t = e / L; pos = e - t * L; } else { pos = e / T; t = e - pos * T; }
+    const int o = Op::kLM ? blockIdx.x * T + t : blockIdx.y;
+    const int x = Op::kLM ? 0 : blockIdx.x * T + t;
+    if (op.valid(o, x)) op.spectral(o, x, pos, tile[e], acc);
+  }
+  __syncthreads();
+  if (Op::kSecond) fft_tile<R, -Op::kSign1, Op::kLM>(tile, tw, f, T);
+  for (int e = threadIdx.x; e < T * L; e += kThreads) {
+    int t, pos;
+    if (Op::kLM) { t = e / L; pos = e - t * L; } else { pos = e / T; t = e - pos * T; }
+    const int o = Op::kLM ? blockIdx.x * T + t : blockIdx.y;
+    const int x = Op::kLM ? 0 : blockIdx.x * T + t;
+    if (op.valid(o, x)) op.store(o, x, pos, tile[e], acc);
+  }
+  if (Op::kRed > 0) reduce_out<R, NR>(acc, op.part, op.pstride);
+}
+
+// ------------------------------------------------------------ dispatch
+inline bool fast_len(int L) { return L >= 16 && L <= 1024 && (L & (L - 1)) == 0; }
+
+inline int ceil_div_l(long a, long b) { return (int)((a + b - 1) / b); }
+
+// Generic-engine tile sizes (see atkm_internal.cuh).
+template <typename R> inline int gen_lm_tile(int L, long nlines) {
+  int T = TileElems<R>::value / L;
+  if (T < 1) T = 1;
+  while (T > 1 && ceil_div_l(nlines, T) < 2 * 152) T >>= 1;
+  return T;
+}
+template <typename R> inline int gen_col_tile(int L, int X, long outer) {
+  int T = TileElems<R>::value / L;
+  if (T > X) T = X;
+  if (T < 1) T = 1;
+  while (T > 8 && (long)ceil_div_l(X, T) * outer < 2 * 152) T >>= 1;
+  return T;
+}
+
+struct PassGrid {
+  dim3 grid;
+  int T;
+  bool fast;
+};
+
+// LM passes: `lines` lines; strided passes: `X` columns x `outer` outer indices.
+template <typename R> inline PassGrid pass_grid(int L, bool LM, long lines, int X, int outer) {
+  PassGrid pg;
+  pg.fast = fast_len(L);
+  if (pg.fast) pg.T = kFastElems / L;
+  else pg.T = LM ? gen_lm_tile<R>(L, lines) : gen_col_tile<R>(L, X, outer);
+  if (LM) pg.grid = dim3(ceil_div_l(lines, pg.T), 1, 1);
+  else pg.grid = dim3(ceil_div_l(X, pg.T), outer, 1);
+  return pg;
+}
+
+template <typename K> inline cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, int L, class Op>
+inline cudaError_t launch_fast_L(const Op& op, const FftLen& f, const PassGrid& pg, cudaStream_t st) {
+  static bool prepared = false;
+  const size_t sm = FastSmem<R, L>::bytes;
+  if (!prepared) {
+    cudaError_t e = set_smem(k_fast<R, L, Op>, sm);
+    if (e != cudaSuccess) return e;
+    prepared = true;
+  }
+  k_fast<R, L, Op><<<pg.grid, kThreads, sm, st>>>(op, tw_table_host<R>(f));
+  return cudaGetLastError();
+}
+
+template <typename R, class Op>
+inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, cudaStream_t st) {
+  if (pg.fast) {
+    switch (f.L) {
+      case 16: return launch_fast_L<R, 16>(op, f, pg, st);
+      case 32: return launch_fast_L<R, 32>(op, f, pg, st);
+      case 64: return launch_fast_L<R, 64>(op, f, pg, st);
+      case 128: return launch_fast_L<R, 128>(op, f, pg, st);
+      case 256: return launch_fast_L<R, 256>(op, f, pg, st);
+      case 512: return launch_fast_L<R, 512>(op, f, pg, st);
+      default: return launch_fast_L<R, 1024>(op, f, pg, st);
+    }
+  }
+  static bool prepared = false;
+  if (!prepared) {
+    cudaError_t e = set_smem(k_generic<R, Op>, (size_t)(TileElems<R>::value + kMaxLen) * sizeof(cx<R>));
+    if (e != cudaSuccess) return e;
+    prepared = true;
+  }
+  const size_t sm = (size_t)(pg.T * f.L + f.L) * sizeof(cx<R>);
+  k_generic<R, Op><<<pg.grid, kThreads, sm, st>>>(op, f, pg.T);
+  return cudaGetLastError();
+}
+
+// ================================================================ ops
+// ---- ATKM (twofold-padded grid).  W1: [Nz][Ny][Mx], W2: [Nz][My][Mx].
+// x forward: lines o = z Ny + y; density formed on the fly, zero for x >= Nx.
+template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
+  const double* a; const double* b; cx<R>* W1; Cst<R> c;
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  __device__ cx<R> load(int o, int, int pos) const {
+    if (pos >= c.Nx) return czero<R>();
+    const size_t idx = (size_t)o * c.Nx + pos;
+    R v;
+    if (MODE == SRC_RHO) {
+      v = (R)a[idx];
+    } else if (MODE == SRC_PSI) {
+      const cx<R> z = from64<R>(reinterpret_cast<const double2*>(a)[idx]);
+      v = z.x * z.x + z.y * z.y;
+    } else {
+      const cx<R> u = from64<R>(reinterpret_cast<const double2*>(a)[idx]);
+      const cx<R> w = from64<R>(reinterpret_cast<const double2*>(b)[idx]);
+      v = u.x * w.x + u.y * w.y;
+    }
+    return mk<R>(v, (R)0);
+  }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int, int pos, cx<R> v, R*) const { W1[(size_t)o * c.Mx + pos] = v; }
+};
+
+// y forward: o = z, x = kx; rows y < Ny of W1, zero beyond.
+template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
+  const cx<R>* W1; cx<R>* W2; Cst<R> c;
+  __device__ bool valid(int, int x) const { return x < c.Mx; }
+  __device__ cx<R> load(int o, int x, int pos) const {
+    return pos < c.Ny ? W1[((size_t)o * c.Ny + pos) * c.Mx + x] : czero<R>();
+  }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const { W2[((size_t)o * c.My + pos) * c.Mx + x] = v; }
+};
+
+// z forward * K / (Mx My Mz) * inverse: o = ky, x = kx; rows z < Nz in and out.
+template <typename R> struct OpAtkmZ : OpBase<-1, true, 0, false> {
+  cx<R>* W2; const R* U0; Cst<R> c; R n0, n1, n2, invM;
+  __device__ bool valid(int, int x) const { return x < c.Mx; }
+  __device__ cx<R> load(int o, int x, int pos) const {
+    return pos < c.Nz ? W2[((size_t)pos * c.My + o) * c.Mx + x] : czero<R>();
+  }
+  __device__ void spectral(int o, int x, int k, cx<R>& v, R*) const {
+    const int kx = kfreq(x, c.Mx), ky = kfreq(o, c.My), kz = kfreq(k, c.Mz);
+    const R nd = n0 * ((R)kx * c.pkx) + n1 * ((R)ky * c.pky) + n2 * ((R)kz * c.pkz);
+    const R u = U0[((size_t)iabs(kz) * (c.Ny + 1) + iabs(ky)) * (c.Nx + 1) + iabs(kx)];
+    v = scl<R>(v, ((R)3 * nd * nd * u - (R)1) * invM);
+  }
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const {
+    if (pos < c.Nz) W2[((size_t)pos * c.My + o) * c.Mx + x] = v;
+  }
+};
+
+// y inverse: o = z, x = kx; output rows y < Ny into W1.
+template <typename R> struct OpAtkmYI : OpBase<1, false, 0, false> {
+  const cx<R>* W2; cx<R>* W1; Cst<R> c;
+  __device__ bool valid(int, int x) const { return x < c.Mx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return W2[((size_t)o * c.My + pos) * c.Mx + x]; }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const {
+    if (pos < c.Ny) W1[((size_t)o * c.Ny + pos) * c.Mx + x] = v;
+  }
+};
+
+// x inverse: lines o; Phi = Re(.) for x < Nx.
+template <typename R> struct OpAtkmXI : OpBase<1, false, 0, true> {
+  const cx<R>* W1; double* phi; Cst<R> c;
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  __device__ cx<R> load(int o, int, int pos) const { return W1[(size_t)o * c.Mx + pos]; }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int, int pos, cx<R> v, R*) const {
+    if (pos < c.Nx) phi[(size_t)o * c.Nx + pos] = (double)v.x;
+  }
+};
+
+// ---- H_phi f (unpadded grid); acc: [Nz][Ny][Nx] kinetic+rotation accumulator.
+// x: multiplier nu^2/2 + Omega y nu on lines o = z Ny + y.
+template <typename R, bool RED> struct OpHX : OpBase<-1, true, RED ? 2 : 0, true> {
+  const double2* f; cx<R>* acc; Cst<R> c; R Omega;
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  __device__ cx<R> load(int o, int, int pos) const { return from64<R>(f[(size_t)o * c.Nx + pos]); }
+  __device__ void spectral(int o, int, int k, cx<R>& v, R* a) const {
+    const R invL = (R)1 / (R)c.Nx;
+    const R nu = (R)kfreq(k, c.Nx) * c.kx;
+    const R y = -c.Ly + (R)(o % c.Ny) * c.hy;
+    const R mkin = (R)0.5 * nu * nu, mrot = Omega * y * nu;
+    if (RED) {
+      const R a2 = (v.x * v.x + v.y * v.y) * invL;
+      a[0] += mkin * a2;
+      a[1] += mrot * a2;
+    }
+    v = scl<R>(v, (mkin + mrot) * invL);
+  }
+  __device__ void store(int o, int, int pos, cx<R> v, R*) const { acc[(size_t)o * c.Nx + pos] = v; }
+};
+
+// y: multiplier nu^2/2 - Omega x nu on lines (o = z, x); acc += result.
+template <typename R, bool RED> struct OpHY : OpBase<-1, true, RED ? 2 : 0, false> {
+  const double2* f; cx<R>* acc; Cst<R> c; R Omega;
+  __device__ bool valid(int, int x) const { return x < c.Nx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)o * c.Ny + pos) * c.Nx + x]); }
+  __device__ void spectral(int, int x, int k, cx<R>& v, R* a) const {
+    const R invL = (R)1 / (R)c.Ny;
+    const R nu = (R)kfreq(k, c.Ny) * c.ky;
+    const R xc = -c.Lx + (R)x * c.hx;
+    const R mkin = (R)0.5 * nu * nu, mrot = -Omega * xc * nu;
+    if (RED) {
+      const R a2 = (v.x * v.x + v.y * v.y) * invL;
+      a[0] += mkin * a2;
+      a[1] += mrot * a2;
+    }
+    v = scl<R>(v, (mkin + mrot) * invL);
+  }
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const {
+    const size_t idx = ((size_t)o * c.Ny + pos) * c.Nx + x;
+    acc[idx] = add<R>(acc[idx], v);
+  }
+};
+
+// z: multiplier nu^2/2 on lines (o = y, x), then
+// Hf = acc + result + (V + beta |phi|^2 + lambda Phi) f.
+// Reductions: kin_z, sum V|f|^2, sum |f|^4, sum Phi |f|^2, sum Re(Hf conj f), sum |f|^2.
+template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, false> {
+  const double2* f; const double2* phi; const double* Phi; const cx<R>* acc; double2* Hf; Cst<R> c; PhysR<R> ph;
+  __device__ bool valid(int, int x) const { return x < c.Nx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)pos * c.Ny + o) * c.Nx + x]); }
+  __device__ void spectral(int, int, int k, cx<R>& v, R* a) const {
+    const R invL = (R)1 / (R)c.Nz;
+    const R nu = (R)kfreq(k, c.Nz) * c.kz;
+    const R m = (R)0.5 * nu * nu;
+    if (RED) a[0] += m * (v.x * v.x + v.y * v.y) * invL;
+    v = scl<R>(v, m * invL);
+  }
+  __device__ void store(int o, int x, int pos, cx<R> v, R* a) const {
+    const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
+    const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
+    const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
+    const cx<R> fv = from64<R>(f[idx]), pv = from64<R>(phi[idx]);
+    const R Pd = (R)Phi[idx];
+    const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
+    const cx<R> kin = add<R>(acc[idx], v);
+    const R ox = kin.x + w * fv.x, oy = kin.y + w * fv.y;
+    Hf[idx] = make_double2((double)ox, (double)oy);
+    if (RED) {
+      const R f2 = fv.x * fv.x + fv.y * fv.y;
+      a[1] += V * f2;
+      a[2] += f2 * f2;
+      a[3] += Pd * f2;
+      a[4] += ox * fv.x + oy * fv.y;
+      a[5] += f2;
+    }
+  }
+};
+
+// ---- preconditioner (unpadded grid); Wk: [Nz][Ny][Nx] workspace.
+template <typename R>
+__device__ __forceinline__ R pv_rsqrt(const Cst<R>& c, const PhysR<R>& ph, R alpha, int x, int y, int z, double2 p64,
+                                      double Pd64) {
+  const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)y * c.hy, zc = -c.Lz + (R)z * c.hz;
+  const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
+  const cx<R> pv = from64<R>(p64);
+  const R Pd = (R)Pd64;
+  const R den = alpha + V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + fabs(ph.lambda) * (Pd > (R)0 ? Pd : (R)0);
+  return rsq<R>(den);
+}
+
+template <typename R> struct OpPXF : OpBase<-1, false, 0, true> {
+  const double2* r; const double2* phi; const double* Phi; cx<R>* Wk; Cst<R> c; PhysR<R> ph; const double* alpha;
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  __device__ cx<R> load(int o, int, int pos) const {
+    const size_t idx = (size_t)o * c.Nx + pos;
+    const R w = pv_rsqrt<R>(c, ph, (R)*alpha, pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
+    return scl<R>(from64<R>(r[idx]), w);
+  }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int, int pos, cx<R> v, R*) const { Wk[(size_t)o * c.Nx + pos] = v; }
+};
+
+template <typename R, int S> struct OpPY : OpBase<S, false, 0, false> {
+  cx<R>* Wk; Cst<R> c;
+  __device__ bool valid(int, int x) const { return x < c.Nx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return Wk[((size_t)o * c.Ny + pos) * c.Nx + x]; }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const { Wk[((size_t)o * c.Ny + pos) * c.Nx + x] = v; }
+};
+
+// z forward * 1/((alpha + |nu|^2/2) N) * inverse on lines (o = y, x).
+template <typename R> struct OpPZ : OpBase<-1, true, 0, false> {
+  cx<R>* Wk; Cst<R> c; const double* alpha;
+  __device__ bool valid(int, int x) const { return x < c.Nx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return Wk[((size_t)pos * c.Ny + o) * c.Nx + x]; }
+  __device__ void spectral(int o, int x, int k, cx<R>& v, R*) const {
+    const R invN = (R)1 / ((R)c.Nx * (R)c.Ny * (R)c.Nz);
+    const R nux = (R)kfreq(x, c.Nx) * c.kx, nuy = (R)kfreq(o, c.Ny) * c.ky, nuz = (R)kfreq(k, c.Nz) * c.kz;
+    v = scl<R>(v, invN / ((R)*alpha + (R)0.5 * (nux * nux + nuy * nuy + nuz * nuz)));
+  }
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const { Wk[((size_t)pos * c.Ny + o) * c.Nx + x] = v; }
+};
+
+template <typename R> struct OpPXI : OpBase<1, false, 0, true> {
+  const cx<R>* Wk; const double2* phi; const double* Phi; double2* Pr; Cst<R> c; PhysR<R> ph; const double* alpha;
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  __device__ cx<R> load(int o, int, int pos) const { return Wk[(size_t)o * c.Nx + pos]; }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int, int pos, cx<R> v, R*) const {
+    const size_t idx = (size_t)o * c.Nx + pos;
+    const R w = pv_rsqrt<R>(c, ph, (R)*alpha, pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
+    Pr[idx] = make_double2((double)(w * v.x), (double)(w * v.y));
+  }
+};
+
+}  // namespace atkm

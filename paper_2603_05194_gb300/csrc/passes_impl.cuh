@@ -1,0 +1,195 @@
+// Launchers of the three spectral operators for one arithmetic type R (the
+// translation units passes_f64.cu and passes_f32.cu instantiate them).
+#pragma once
+
+#include <math.h>
+
+#include "ops.cuh"
+
+namespace atkm {
+
+template <typename R> inline cx<R>* ws1(atkm_plan* p);
+template <> inline double2* ws1<double>(atkm_plan* p) { return p->W1; }
+template <> inline float2* ws1<float>(atkm_plan* p) { return p->W1f; }
+template <typename R> inline cx<R>* ws2(atkm_plan* p);
+template <> inline double2* ws2<double>(atkm_plan* p) { return p->W2; }
+template <> inline float2* ws2<float>(atkm_plan* p) { return p->W2f; }
+template <typename R> inline cx<R>* ws3(atkm_plan* p);
+template <> inline double2* ws3<double>(atkm_plan* p) { return p->T1; }
+template <> inline float2* ws3<float>(atkm_plan* p) { return p->T1f; }
+template <typename R> inline const R* u0tab(atkm_plan* p);
+template <> inline const double* u0tab<double>(atkm_plan* p) { return p->U0; }
+template <> inline const float* u0tab<float>(atkm_plan* p) { return p->U0f; }
+
+template <typename R> inline const char* nm(const char* d, const char* f) { return sizeof(R) == 8 ? d : f; }
+inline double fftflops(double n) { return 5.0 * n * log2(n); }
+
+#define ATKM_RUN(NAME, BYTES, FLOPS, OP, FLEN, PG)              \
+  do {                                                         \
+    prof_begin(p, NAME, BYTES, FLOPS, st);                     \
+    cudaError_t e_ = run_pass<R>(OP, FLEN, PG, st);            \
+    prof_end(p, st);                                           \
+    count_launches(1);                                         \
+    if (e_ != cudaSuccess) return e_;                          \
+  } while (0)
+
+template <typename R>
+cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b, double* phi, cudaStream_t st) {
+  const Geo& g = p->g;
+  cx<R>* W1 = ws1<R>(p);
+  cx<R>* W2 = ws2<R>(p);
+  const R* U0 = u0tab<R>(p);
+  if (!W1 || !W2 || !U0) return cudaErrorInvalidValue;
+  const Cst<R> c = make_cst<R>(g);
+  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const double inb = mode == SRC_RHO ? 8.0 : (mode == SRC_PSI ? 16.0 : 32.0);
+  const double fx = (double)g.Nz * g.Ny * fftflops(g.Mx), fy = (double)g.Nz * g.Mx * fftflops(g.My);
+  const double fz = 2.0 * g.My * g.Mx * fftflops(g.Mz);
+  const double u0b = (double)sizeof(R) * (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
+  const long nl = (long)g.Nz * g.Ny;
+  // x forward
+  const PassGrid gx = pass_grid<R>(g.Mx, true, nl, 0, 0);
+  const char* nx = nm<R>("atkm_x_fwd_f64", "atkm_x_fwd_f32");
+  if (mode == SRC_RHO) {
+    OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = W1; op.c = c;
+    ATKM_RUN(nx, inb * N + 2 * N * s, fx, op, p->fM[0], gx);
+  } else if (mode == SRC_PSI) {
+    OpAtkmXF<R, SRC_PSI> op; op.a = a; op.b = b; op.W1 = W1; op.c = c;
+    ATKM_RUN(nx, inb * N + 2 * N * s, fx, op, p->fM[0], gx);
+  } else {
+    OpAtkmXF<R, SRC_PAIR> op; op.a = a; op.b = b; op.W1 = W1; op.c = c;
+    ATKM_RUN(nx, inb * N + 2 * N * s, fx, op, p->fM[0], gx);
+  }
+  // y forward
+  {
+    OpAtkmYF<R> op; op.W1 = W1; op.W2 = W2; op.c = c;
+    const PassGrid pg = pass_grid<R>(g.My, false, 0, g.Mx, g.Nz);
+    ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32"), 6 * N * s, fy, op, p->fM[1], pg);
+  }
+  // z forward * K * inverse
+  {
+    OpAtkmZ<R> op; op.W2 = W2; op.U0 = U0; op.c = c;
+    op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
+    op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
+    const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Mx, g.My);
+    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32"), 8 * N * s + u0b, fz, op, p->fM[2], pg);
+  }
+  // y inverse
+  {
+    OpAtkmYI<R> op; op.W2 = W2; op.W1 = W1; op.c = c;
+    const PassGrid pg = pass_grid<R>(g.My, false, 0, g.Mx, g.Nz);
+    ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32"), 6 * N * s, fy, op, p->fM[1], pg);
+  }
+  // x inverse
+  {
+    OpAtkmXI<R> op; op.W1 = W1; op.phi = phi; op.c = c;
+    ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32"), 2 * N * s + 8 * N, fx, op, p->fM[0], gx);
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double* phi, const double* Phi, double* Hf,
+                     int red_slot, cudaStream_t st) {
+  const Geo& g = p->g;
+  cx<R>* acc = ws3<R>(p);
+  if (!acc) return cudaErrorInvalidValue;
+  const bool red = red_slot >= 0;
+  const Cst<R> c = make_cst<R>(g);
+  const PhysR<R> pr = make_physr<R>(ph);
+  const double2* fin = reinterpret_cast<const double2*>(f);
+  const double2* pin = reinterpret_cast<const double2*>(phi);
+  double2* out = reinterpret_cast<double2*>(Hf);
+  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const long nl = (long)g.Nz * g.Ny;
+  cudaError_t e;
+  // x
+  {
+    const PassGrid pg = pass_grid<R>(g.Nx, true, nl, 0, 0);
+    const double fl = 2.0 * nl * fftflops(g.Nx);
+    const char* n = nm<R>("H_x_f64", "H_x_f32");
+    if (red) {
+      OpHX<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
+      ATKM_RUN(n, 16 * N + N * s, fl, op, p->fN[0], pg);
+      if ((e = launch_finalize(p, 2, pg.grid.x * pg.grid.y, red_slot + 0, st)) != cudaSuccess) return e;
+    } else {
+      OpHX<R, false> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      ATKM_RUN(n, 16 * N + N * s, fl, op, p->fN[0], pg);
+    }
+  }
+  // y
+  {
+    const PassGrid pg = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
+    const double fl = 2.0 * g.Nz * g.Nx * fftflops(g.Ny);
+    const char* n = nm<R>("H_y_f64", "H_y_f32");
+    if (red) {
+      OpHY<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
+      ATKM_RUN(n, 16 * N + 2 * N * s, fl, op, p->fN[1], pg);
+      if ((e = launch_finalize(p, 2, pg.grid.x * pg.grid.y, red_slot + 2, st)) != cudaSuccess) return e;
+    } else {
+      OpHY<R, false> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      ATKM_RUN(n, 16 * N + 2 * N * s, fl, op, p->fN[1], pg);
+    }
+  }
+  // z + pointwise
+  {
+    const PassGrid pg = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
+    const double fl = 2.0 * g.Ny * g.Nx * fftflops(g.Nz);
+    const char* n = nm<R>("H_z_f64", "H_z_f32");
+    if (red) {
+      OpHZ<R, true> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
+      op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
+      ATKM_RUN(n, 56 * N + N * s, fl, op, p->fN[2], pg);
+      if ((e = launch_finalize(p, 6, pg.grid.x * pg.grid.y, red_slot + 4, st)) != cudaSuccess) return e;
+    } else {
+      OpHZ<R, false> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
+      ATKM_RUN(n, 56 * N + N * s, fl, op, p->fN[2], pg);
+    }
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev, const double* r, const double* phi,
+                           const double* Phi, double* Pr, cudaStream_t st) {
+  const Geo& g = p->g;
+  cx<R>* Wk = ws3<R>(p);
+  if (!Wk) return cudaErrorInvalidValue;
+  const Cst<R> c = make_cst<R>(g);
+  const PhysR<R> pr = make_physr<R>(ph);
+  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const long nl = (long)g.Nz * g.Ny;
+  const double fx = (double)nl * fftflops(g.Nx), fy = (double)g.Nz * g.Nx * fftflops(g.Ny);
+  const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
+  const PassGrid gy = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
+  const PassGrid gz = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
+  {
+    OpPXF<R> op; op.r = reinterpret_cast<const double2*>(r); op.phi = reinterpret_cast<const double2*>(phi);
+    op.Phi = Phi; op.Wk = Wk; op.c = c; op.ph = pr; op.alpha = alpha_dev;
+    ATKM_RUN(nm<R>("P_x_fwd_f64", "P_x_fwd_f32"), 40 * N + N * s, fx, op, p->fN[0], gx);
+  }
+  {
+    OpPY<R, -1> op; op.Wk = Wk; op.c = c;
+    ATKM_RUN(nm<R>("P_y_f64", "P_y_f32"), 2 * N * s, fy, op, p->fN[1], gy);
+  }
+  {
+    OpPZ<R> op; op.Wk = Wk; op.c = c; op.alpha = alpha_dev;
+    ATKM_RUN(nm<R>("P_z_f64", "P_z_f32"), 2 * N * s, 2.0 * g.Ny * g.Nx * fftflops(g.Nz), op, p->fN[2], gz);
+  }
+  {
+    OpPY<R, 1> op; op.Wk = Wk; op.c = c;
+    ATKM_RUN(nm<R>("P_y_f64", "P_y_f32"), 2 * N * s, fy, op, p->fN[1], gy);
+  }
+  {
+    OpPXI<R> op; op.Wk = Wk; op.phi = reinterpret_cast<const double2*>(phi); op.Phi = Phi;
+    op.Pr = reinterpret_cast<double2*>(Pr); op.c = c; op.ph = pr; op.alpha = alpha_dev;
+    ATKM_RUN(nm<R>("P_x_inv_f64", "P_x_inv_f32"), 40 * N + N * s, fx, op, p->fN[0], gx);
+  }
+  return cudaSuccess;
+}
+
+#undef ATKM_RUN
+
+}  // namespace atkm

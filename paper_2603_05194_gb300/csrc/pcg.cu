@@ -165,6 +165,7 @@ int red_grid(size_t N) {
 
 cudaError_t launch_finalize(atkm_plan* p, int nslots, int nblocks, int dst_slot, cudaStream_t st) {
   k_finalize<<<nslots, kRedThreads, 0, st>>>(p->partials, nblocks, p->scal + dst_slot);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -174,6 +175,10 @@ struct PcgBuffers {
   double2 *phi = nullptr, *Hphi = nullptr, *r = nullptr, *Pr = nullptr, *p = nullptr, *pprev = nullptr,
           *rprev = nullptr, *Hp = nullptr, *phin = nullptr;
   double *Phi = nullptr, *Phi1 = nullptr, *Phin = nullptr;
+  // scalar state carried between calls (resume)
+  bool valid = false, f32 = false, have_prev = false, force_sd = true;
+  int n = 0, caps = 0;
+  double E = 0.0, den_prev = 0.0, linf = INFINITY;
 };
 
 void pcg_free(atkm_plan* p) {
@@ -202,7 +207,12 @@ static cudaError_t pcg_alloc(atkm_plan* p) {
     cudaError_t e = dev_alloc(p, (void**)q, N * sizeof(double));
     if (e != cudaSuccess) { pcg_free(p); return e; }
   }
-  return cudaSuccess;
+  // the previous-iteration vectors are read (and ignored) before the first
+  // step; give them defined contents
+  cudaError_t e = cudaMemset(b->pprev, 0, N * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemset(b->rprev, 0, N * sizeof(double2));
+  if (e != cudaSuccess) pcg_free(p);
+  return e;
 }
 
 // Small helper bundling plan, stream and the scalar read-back.
@@ -220,6 +230,7 @@ struct Dev {
     for (auto& pr : pairs) { dp.u[dp.n] = pr.first; dp.v[dp.n] = pr.second; ++dp.n; }
     const int G = red_grid(N);
     k_dots<<<G, kRedThreads, 0, st>>>(dp, N, p->partials);
+    count_launches(1);
     chk(cudaGetLastError());
     chk(launch_finalize(p, dp.n, G, dst, st));
   }
@@ -227,6 +238,7 @@ struct Dev {
                double c2, const double2* w, int dst) {
     const int G = red_grid(N);
     k_lincomb<<<G, kRedThreads, 0, st>>>(out, v0, c0, v1, c1, v2, c2, w, N, p->partials);
+    count_launches(1);
     chk(cudaGetLastError());
     chk(launch_finalize(p, 2, G, dst, st));
   }
@@ -301,6 +313,7 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
   if (Pr == r || Pr == phi || Pr == Phi) return fail(plan, ATKM_ERR_ARG, "apply_preconditioner: output aliases an input");
   cudaStream_t st = (cudaStream_t)stream;
   k_set_scalar<<<1, 1, 0, st>>>(plan->scal + SC_ALPHA, alpha);
+  count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_precond<double>(plan, make_phys(prm), plan->scal + SC_ALPHA, r, phi, Phi, Pr, st);
   return e == cudaSuccess ? ATKM_OK : cuda_fail(plan, e, "apply_preconditioner");
@@ -350,22 +363,35 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
     return cuda_fail(plan, d.err, "pcg_ground_state");
   };
 
-  // Normalise psi0 into phi.
-  const double2* psi = reinterpret_cast<const double2*>(psi_inout);
-  d.dots({{psi, psi}}, S_N);
-  d.fetch(S_N, S_N + 1);
-  if (d.err != cudaSuccess) return fail_cuda();
-  const double n0 = sqrt(hv * d.h(S_N));
-  if (!(n0 > 0.0) || !isfinite(n0)) {
-    out->status = ATKM_ERR_NAN;
-    return fail(plan, ATKM_ERR_NAN, "pcg_ground_state: initial state has zero or non-finite norm");
-  }
-  d.lincomb(B.phi, psi, 1.0 / n0, nullptr, 0, nullptr, 0, nullptr, S_T);
-  ATKM(SRC_PSI, (const double*)B.phi, nullptr, B.Phi);
-
   double E = 0.0, den_prev = 0.0, linf = INFINITY;
   bool have_E = false, force_sd = true, have_prev = false;
   int caps = 0, n = 0, status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0;
+  int n_start = 0;
+  double f32_best = INFINITY;
+  int f32_best_n = 0;
+  if (opts->resume && B.valid) {
+    // continue the previous solve of this plan
+    f32 = B.f32 && mixed;
+    if (B.f32 && !mixed) ATKM(SRC_PSI, (const double*)B.phi, nullptr, B.Phi);  // FP64 from here on
+    have_E = !(B.f32 && !mixed);
+    E = B.E; den_prev = B.den_prev; linf = B.linf; force_sd = B.force_sd || (B.f32 && !mixed);
+    have_prev = B.have_prev; caps = B.caps; n = n_start = f32_best_n = B.n;
+  } else {
+    // Normalise psi0 into phi.
+    const double2* psi = reinterpret_cast<const double2*>(psi_inout);
+    d.dots({{psi, psi}}, S_N);
+    d.fetch(S_N, S_N + 1);
+    if (d.err != cudaSuccess) return fail_cuda();
+    const double n0 = sqrt(hv * d.h(S_N));
+    if (!(n0 > 0.0) || !isfinite(n0)) {
+      out->status = ATKM_ERR_NAN;
+      B.valid = false;
+      return fail(plan, ATKM_ERR_NAN, "pcg_ground_state: initial state has zero or non-finite norm");
+    }
+    d.lincomb(B.phi, psi, 1.0 / n0, nullptr, 0, nullptr, 0, nullptr, S_T);
+    ATKM(SRC_PSI, (const double*)B.phi, nullptr, B.Phi);
+  }
+  B.valid = false;  // set again when this call ends cleanly
   Parts q{};
   double mu = 0.0, res = 0.0;
   int logc = 0;
@@ -391,7 +417,11 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
       ++logc;
     }
     if (!isfinite(E) || !isfinite(res) || !isfinite(mu)) { status = ATKM_ERR_NAN; break; }
-    if (f32 && (res <= opts->switch_tol || caps >= 2)) {
+    if (f32) {
+      // FP32 stagnation: no halving of the best residual within 100 iterations
+      if (res < 0.5 * f32_best) { f32_best = res; f32_best_n = n; }
+    }
+    if (f32 && (res <= opts->switch_tol || caps >= 2 || n - f32_best_n > 100)) {
       // hand over to FP64: recompute Phi and H phi in FP64, restart the direction
       f32 = false;
       caps = 0;
@@ -405,11 +435,12 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
       status = ATKM_OK;
       break;
     }
-    if (n >= opts->max_iter) { status = ATKM_NOT_CONVERGED; break; }
+    if (n - n_start >= opts->max_iter) { status = ATKM_NOT_CONVERGED; break; }
     if (f32) ++f32_iters;
     // ---- Step 3: preconditioned PR+ direction
     const double alpha = q.kin + q.pot + beta * q.f4 + fabs(lam * q.dip);
     k_set_scalar<<<1, 1, 0, d.st>>>(plan->scal + SC_ALPHA, alpha);
+  count_launches(1);
     d.chk(cudaGetLastError());
     PREC();
     d.dots({{B.Pr, B.phi}, {B.r, B.Pr}, {B.r, B.phi}, {B.rprev, B.Pr}, {B.rprev, B.phi}, {B.pprev, B.phi},
@@ -451,6 +482,7 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
     {
       const int G = red_grid(B.N);
       k_curv_sums<<<G, kRedThreads, 0, d.st>>>(B.phi, B.p, B.Phi, B.Phi1, beta, lam, B.N, plan->partials);
+      count_launches(1);
       d.chk(cudaGetLastError());
       d.chk(launch_finalize(plan, 3, G, S_C + 1, d.st));
     }
@@ -475,11 +507,14 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
       const double nrm2 = hv * d.h(S_T);
       const int G = red_grid(B.N);
       k_scale_linf<<<G, kRedThreads, 0, d.st>>>(B.phin, B.phi, 1.0 / sqrt(nrm2), B.N, plan->partials);
+      count_launches(1);
       d.chk(cudaGetLastError());
       k_finalize_max<<<1, kRedThreads, 0, d.st>>>(plan->partials, G, plan->scal + S_L);
+      count_launches(1);
       d.chk(cudaGetLastError());
       ATKM(SRC_PSI, (const double*)B.phin, nullptr, B.Phin);
       k_quartic_sums<<<G, kRedThreads, 0, d.st>>>(B.phin, B.Phin, B.N, plan->partials);
+      count_launches(1);
       d.chk(cudaGetLastError());
       d.chk(launch_finalize(plan, 2, G, S_Q, d.st));
       d.fetch(S_Q, S_L + 1);
@@ -536,7 +571,10 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
       break;
     }
   }
-  // Copy the state back and report.
+  // Keep the scalar state for a later resume, copy the state back and report.
+  B.valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED);
+  B.f32 = f32; B.have_prev = have_prev; B.force_sd = force_sd; B.n = n; B.caps = caps;
+  B.E = E; B.den_prev = den_prev; B.linf = linf;
   d.chk(cudaMemcpyAsync(psi_inout, B.phi, B.N * sizeof(double2), cudaMemcpyDeviceToDevice, d.st));
   d.chk(cudaStreamSynchronize(d.st));
   if (d.err != cudaSuccess) return fail_cuda();

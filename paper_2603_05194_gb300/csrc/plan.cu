@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "atkm_internal.cuh"
@@ -31,6 +32,9 @@
 namespace atkm {
 
 thread_local std::string g_last_error;
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 int fail(atkm_plan* p, int code, const std::string& msg) {
   g_last_error = msg;
@@ -177,6 +181,26 @@ __global__ void k_U0(double* __restrict__ U0, const double* __restrict__ Tx, con
   }
 }
 
+// Full padded multiplier K(k) = -1 + 3 (n.nu)^2 U0 in FFT order.
+__global__ void k_multiplier_full(double* __restrict__ K, const double* __restrict__ U0, Geo g, double n0, double n1,
+                                  double n2) {
+  const size_t total = (size_t)g.Mx * g.My * g.Mz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.Mx);
+    const int y = (int)((i / g.Mx) % g.My);
+    const int z = (int)(i / ((size_t)g.Mx * g.My));
+    const int kx = x < g.Mx / 2 ? x : x - g.Mx, ky = y < g.My / 2 ? y : y - g.My, kz = z < g.Mz / 2 ? z : z - g.Mz;
+    const double nd = n0 * kPi * kx / (2.0 * g.Lx) + n1 * kPi * ky / (2.0 * g.Ly) + n2 * kPi * kz / (2.0 * g.Lz);
+    const double u = U0[((size_t)abs(kz) * (g.Ny + 1) + abs(ky)) * (g.Nx + 1) + abs(kx)];
+    K[i] = -1.0 + 3.0 * nd * nd * u;
+  }
+}
+
+__global__ void k_to_f32(float* __restrict__ dst, const double* __restrict__ src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 bool smooth235(int n) {
   if (n <= 0) return false;
   for (int r : {2, 3, 5})
@@ -201,7 +225,7 @@ bool make_fft_len(int L, FftLen& f) {
 }
 
 void free_plan_memory(atkm_plan* p) {
-  void* ptrs[] = {p->tw64, p->tw32, p->U0, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f, p->partials, p->scal};
+  void* ptrs[] = {p->tw64, p->tw32, p->U0, p->U0f, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f, p->partials, p->scal};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->scal_host) cudaFreeHost(p->scal_host);
@@ -210,6 +234,50 @@ void free_plan_memory(atkm_plan* p) {
 }  // namespace
 
 void pcg_free(atkm_plan* p);  // pcg.cu
+
+// Event-pair record of pass launches (opt-in measurement support).
+struct Profiler {
+  struct Rec {
+    const char* name;
+    double bytes, flops;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  bool open = false;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+void prof_begin(atkm_plan* p, const char* name, double bytes, double flops, cudaStream_t st) {
+  Profiler* pr = p->prof;
+  if (!pr) return;
+  Profiler::Rec r{name, bytes, flops, pr->get(), nullptr};
+  if (!r.a) return;
+  cudaEventRecord(r.a, st);
+  pr->recs.push_back(r);
+  pr->open = true;
+}
+
+void prof_end(atkm_plan* p, cudaStream_t st) {
+  Profiler* pr = p->prof;
+  if (!pr || !pr->open) return;
+  pr->open = false;
+  cudaEvent_t b = pr->get();
+  if (!b) { pr->recs.pop_back(); return; }
+  cudaEventRecord(b, st);
+  pr->recs.back().b = b;
+}
 
 }  // namespace atkm
 
@@ -224,10 +292,14 @@ const char* atkm_last_error_string(const atkm_plan* plan) {
 
 unsigned long long atkm_plan_device_bytes(const atkm_plan* plan) { return plan ? plan->bytes : 0ull; }
 
+unsigned long long atkm_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 void atkm_plan_destroy(atkm_plan* plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
   pcg_free(plan);
+  delete plan->prof;
+  delete plan->prof_stopped_;
   free_plan_memory(plan);
   delete plan;
 }
@@ -252,9 +324,9 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   cudaStream_t st = (cudaStream_t)stream;
   atkm_plan* p = new atkm_plan();
   memset(&p->g, 0, sizeof(p->g));
-  p->tw64 = nullptr; p->tw32 = nullptr; p->U0 = nullptr; p->W1 = p->W2 = p->T1 = nullptr;
+  p->tw64 = nullptr; p->tw32 = nullptr; p->U0 = nullptr; p->U0f = nullptr; p->W1 = p->W2 = p->T1 = nullptr;
   p->W1f = p->W2f = p->T1f = nullptr; p->partials = nullptr; p->scal = nullptr; p->scal_host = nullptr;
-  p->pcg = nullptr; p->bytes = 0; p->flags = flags;
+  p->pcg = nullptr; p->prof = nullptr; p->prof_stopped_ = nullptr; p->bytes = 0; p->flags = flags;
   Geo& g = p->g;
   g.Nx = N[0]; g.Ny = N[1]; g.Nz = N[2];
   g.Mx = 2 * N[0]; g.My = 2 * N[1]; g.Mz = 2 * N[2];
@@ -282,6 +354,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
     f.tw64 = p->tw64 + off;
     f.tw32 = p->tw32 + off;
     k_twiddles<<<(lens[i] + 255) / 256, 256, 0, st>>>(p->tw64 + off, p->tw32 + off, lens[i]);
+    count_launches(1);
     off += lens[i];
   }
   // ---- U0 octant
@@ -326,6 +399,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
     }
     k_U0<<<(int)std::min<size_t>((n_oct + 255) / 256, 65535), 256, 0, st>>>(p->U0, d_T[0], d_T[1], d_T[2], d_w, Q,
                                                                           g.Nx, g.Ny, g.Nz, a[0], a[1], a[2], s_c);
+    count_launches(4);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -340,6 +414,9 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
     if ((e = dev_alloc(p, (void**)&p->W1f, 2 * Nt * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
     if ((e = dev_alloc(p, (void**)&p->W2f, 4 * Nt * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
     if ((e = dev_alloc(p, (void**)&p->T1f, Nt * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
+    if ((e = dev_alloc(p, (void**)&p->U0f, n_oct * sizeof(float))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan U0f"));
+    k_to_f32<<<(int)std::min<size_t>((n_oct + 255) / 256, 4096), 256, 0, st>>>(p->U0f, p->U0, n_oct);
+    count_launches(1);
   }
   // reductions: the largest CTA count of a reducing pass, or the vector grid
   long maxb = 1216;
@@ -365,7 +442,9 @@ int atkm_plan_copy_U0(const atkm_plan* plan, double* dst, void* stream) {
 
 int atkm_plan_copy_multiplier(const atkm_plan* plan, double* dst, void* stream) {
   if (!plan || !dst) return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_copy_multiplier: NULL argument");
-  cudaError_t e = launch_multiplier_full(plan, dst, (cudaStream_t)stream);
+  k_multiplier_full<<<1216, 256, 0, (cudaStream_t)stream>>>(dst, plan->U0, plan->g, plan->n[0], plan->n[1], plan->n[2]);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_plan_copy_multiplier");
 }
 
@@ -401,6 +480,58 @@ int apply_H(atkm_plan* plan, const atkm_params* prm, const double* f, const doub
   if (Hf == f || Hf == phi || Hf == Phi) return fail(plan, ATKM_ERR_ARG, "apply_H: output aliases an input");
   cudaError_t e = launch_H<double>(plan, make_phys(prm), f, phi, Phi, Hf, -1, (cudaStream_t)stream);
   return e == cudaSuccess ? ATKM_OK : cuda_fail(plan, e, "apply_H");
+}
+
+int atkm_plan_set_profiling(atkm_plan* plan, int on) {
+  if (!plan) return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_set_profiling: NULL plan");
+  if (on) {
+    if (!plan->prof) {
+      plan->prof = plan->prof_stopped_ ? plan->prof_stopped_ : new Profiler();
+      plan->prof_stopped_ = nullptr;
+    }
+    cudaDeviceSynchronize();
+    plan->prof->recs.clear();
+    plan->prof->used = 0;
+    plan->prof->open = false;
+  } else if (plan->prof) {
+    // keep the record for atkm_plan_kernel_stats; stop recording new launches
+    delete plan->prof_stopped_;
+    plan->prof_stopped_ = plan->prof;
+    plan->prof = nullptr;
+  }
+  return ATKM_OK;
+}
+
+int atkm_plan_kernel_stats(atkm_plan* plan, atkm_kernel_stat* out, int capacity, int* count) {
+  if (!plan || !count || (capacity > 0 && !out)) return fail(plan, ATKM_ERR_ARG, "atkm_plan_kernel_stats: NULL argument");
+  Profiler* pr = plan->prof ? plan->prof : plan->prof_stopped_;
+  *count = 0;
+  if (!pr) return ATKM_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(plan, e, "atkm_plan_kernel_stats");
+  std::vector<atkm_kernel_stat> agg;
+  for (const auto& r : pr->recs) {
+    if (!r.b) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+    int k = -1;
+    for (size_t i = 0; i < agg.size(); ++i)
+      if (strncmp(agg[i].name, r.name, sizeof(agg[i].name)) == 0) k = (int)i;
+    if (k < 0) {
+      atkm_kernel_stat st;
+      memset(&st, 0, sizeof(st));
+      strncpy(st.name, r.name, sizeof(st.name) - 1);
+      agg.push_back(st);
+      k = (int)agg.size() - 1;
+    }
+    agg[k].launches += 1;
+    agg[k].ms_total += ms;
+    agg[k].bytes_total += r.bytes;
+    agg[k].flops_total += r.flops;
+  }
+  *count = (int)agg.size();
+  for (int i = 0; i < capacity && i < (int)agg.size(); ++i) out[i] = agg[i];
+  return ATKM_OK;
 }
 
 }  // extern "C"
