@@ -232,6 +232,33 @@ typedef struct atkm_result {
 int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opts* opts,
                      double* psi_inout, atkm_result* out, void* stream);
 
+/*
+ * atkm_inner_products_noalloc -- out[i] = hvol * Re(sum_j u_i[j] conj(v_i[j]))
+ * for i < npairs, without allocating anything.  The paper has no counterpart:
+ * this is for callers that cannot call cudaMalloc (code inside a host
+ * framework that owns every device allocation, or a process that must not grow
+ * its device footprint after start-up).  With hvol = h_x h_y h_z it is the
+ * discrete inner product <u_i, v_i> of the solver.
+ *   u, v    HOST arrays of npairs DEVICE pointers, each to n interleaved
+ *           complex doubles (16-byte aligned).
+ *   npairs  1 .. ATKM_NOALLOC_MAX_PAIRS (8); anything else is rejected with
+ *           ATKM_ERR_ARG before any work is enqueued.
+ *   n       complex elements per vector (> 0).
+ *   out     DEVICE array of npairs doubles, written stream-ordered.
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * 8 x 1216 doubles (77,824 bytes) that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Every call on a device shares the array: calls
+ * whose kernels overlap on the GPU (different streams, no ordering between
+ * them) race and may return wrong sums; order them on one stream.  Each call
+ * overwrites every partial it reads, so nothing needs clearing between calls.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define ATKM_NOALLOC_MAX_PAIRS 8
+int atkm_inner_products_noalloc(const double* const* u, const double* const* v, int npairs,
+                                unsigned long long n, double hvol, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

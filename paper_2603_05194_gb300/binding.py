@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
         "pcg_ground_state": (ip, [vp, C.POINTER(Params), C.POINTER(PcgOpts), vp, C.POINTER(Result), vp]),
         "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
         "atkm_launch_count": (C.c_ulonglong, []),
+        "atkm_inner_products_noalloc": (ip, [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_ulonglong, C.c_double, vp,
+                                             vp]),
         "atkm_plan_kernel_stats": (ip, [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -106,6 +108,28 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def inner_products_noalloc(us, vs, hvol: float, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """<u_i, v_i> = hvol Re(sum u_i conj v_i) into the device tensor `out`
+    through the allocation-free entry point (see include/atkm.h)."""
+    lib = load_library()
+    n = len(us)
+    if len(vs) != n:
+        raise ValueError("us and vs differ in length")
+    ua = (C.c_void_p * max(n, 1))(*[C.c_void_p(t.data_ptr()) for t in us])
+    va = (C.c_void_p * max(n, 1))(*[C.c_void_p(t.data_ptr()) for t in vs])
+    numel = us[0].numel() if n else 0
+    for t in list(us) + list(vs):
+        if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous() and t.numel() == numel):
+            raise ValueError("vectors must be contiguous complex128 CUDA tensors of equal size")
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= n):
+        raise ValueError("out must be a float64 CUDA tensor with npairs elements")
+    code = lib.atkm_inner_products_noalloc(ua, va, n, numel, float(hvol), C.c_void_p(out.data_ptr()),
+                                           _stream(stream))
+    if code != ATKM_OK:
+        raise AtkmError(code, lib.atkm_last_error_string(None).decode())
+    return out
 
 
 def launch_count() -> int:
