@@ -232,6 +232,8 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NS], double* pa
 // ---------------------------------------------------------------- plan
 struct Geo {
   int Nx, Ny, Nz, Mx, My, Mz;
+  int Xh;  // Nx + 1: x-frequencies 0..Nx kept by the real-data ATKM transform
+  int XS;  // row stride of the half-spectrum workspaces (Xh rounded up to 16)
   double Lx, Ly, Lz, hx, hy, hz;
 };
 
@@ -263,8 +265,8 @@ struct atkm_plan {
   float2* tw32;
   double* U0;          // octant (Nz+1)(Ny+1)(Nx+1)
   float* U0f;          // FP32 copy of U0 (FP32 workspaces only)
-  double2* W1;         // [Nz][Ny][Mx]
-  double2* W2;         // [Nz][My][Mx]
+  double2* W1;         // [Nz][Ny][XS] half spectrum in x
+  double2* W2;         // [Nz][My][XS]
   double2* T1;         // [Nz][Ny][Nx]
   float2* W1f;
   float2* W2f;

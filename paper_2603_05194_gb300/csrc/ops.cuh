@@ -50,7 +50,46 @@ template <typename R> inline PhysR<R> make_physr(const Phys& p) {
 __device__ __forceinline__ int kfreq(int m, int M) { return m < (M >> 1) ? m : m - M; }
 __device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
 
-template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { return mk<R>((R)z.x, (R)z.y); }
+// binary64 <-> binary32 conversions for the FP32 passes done on the integer
+// pipe from the IEEE-754 bit layouts (the hardware conversion instructions
+// share the slow FP64 pipe on this part).  binary64 -> binary32 rounds the 29
+// dropped mantissa bits half-up (a mantissa carry moves into the exponent),
+// flushes results below the binary32 normal range to signed zero and
+// saturates to infinity; binary32 -> binary64 is exact for normal numbers and
+// flushes binary32 subnormals to signed zero.
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned int hi = (unsigned int)(u >> 32);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e >= 255) {
+    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (u & 0x000fffffffffffffull) != 0ull;
+    return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
+  }
+  if (e <= 0) return __uint_as_float(sign);
+  const unsigned long long m = u & 0x000fffffffffffffull;
+  unsigned int bits = ((unsigned int)e << 23) + (unsigned int)((m + (1ull << 28)) >> 29);
+  if (bits >= 0x7f800000u) bits = 0x7f800000u;
+  return __uint_as_float(sign | bits);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned int m = u & 0x7fffffu;
+  unsigned int hi, lo;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  else if (e == 255u) { hi = sign | 0x7ff00000u | (m >> 3); lo = (m & 7u) << 29; }
+  else { hi = sign | ((e + 896u) << 20) | (m >> 3); lo = (m & 7u) << 29; }
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+template <typename R> __device__ __forceinline__ R tor(double v);
+template <> __device__ __forceinline__ double tor<double>(double v) { return v; }
+template <> __device__ __forceinline__ float tor<float>(double v) { return d2f_bits(v); }
+template <typename R> __device__ __forceinline__ double tod(R v);
+template <> __device__ __forceinline__ double tod<double>(double v) { return v; }
+template <> __device__ __forceinline__ double tod<float>(float v) { return f2d_bits(v); }
+template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { return mk<R>(tor<R>(z.x), tor<R>(z.y)); }
 template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R)0, (R)0); }
 
 template <typename R> __device__ __forceinline__ R rsq(R v);
@@ -137,6 +176,7 @@ template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
   static constexpr bool kSecond = SECOND;  // inverse transform after the spectral step
   static constexpr int kRed = NRED;        // fused reduction slots
   static constexpr bool kLM = LM;          // line-major (x) pass
+  static constexpr bool kMirror = false;   // post-processing needs the mirror frequency L - k
   double* part = nullptr;                  // reduction partials [slot][block]
   int pstride = 0;
 };
@@ -173,17 +213,32 @@ __global__ void __launch_bounds__(kThreads) k_fast(Op op, const cx<R>* __restric
 #pragma unroll
   for (int s = 0; s < NR; ++s) acc[s] = (R)0;
   fast_fft<R, L, Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
-  if (ok) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) op.spectral(o, x, j + C::TPL * r, v[r], acc);
-  }
-  if (Op::kSecond) {
+  if constexpr (Op::kMirror) {
+    // exchange so every thread sees the frequency L - k of each of its k
     __syncthreads();
-    fast_fft<R, L, -Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
-  }
-  if (ok) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
+    for (int r = 0; r < 8; ++r) b0[fsa<R, L, Op::kLM>(t, j + C::TPL * r)] = v[r];
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int k = j + C::TPL * r;
+        op.post(o, x, k, v[r], b0[fsa<R, L, Op::kLM>(t, (L - k) & (L - 1))], acc);
+      }
+    }
+  } else {
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) op.spectral(o, x, j + C::TPL * r, v[r], acc);
+    }
+    if (Op::kSecond) {
+      __syncthreads();
+      fast_fft<R, L, -Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
+    }
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
+    }
   }
   if (Op::kRed > 0) reduce_out<R, NR>(acc, op.part, op.pstride);
 }
@@ -208,6 +263,18 @@ __global__ void __launch_bounds__(kThreads) k_generic(Op op, FftLen f, int T) {
   R acc[NR];
 #pragma unroll
   for (int s = 0; s < NR; ++s) acc[s] = (R)0;
+  if constexpr (Op::kMirror) {
+    for (int e = threadIdx.x; e < T * L; e += kThreads) {
+      int t, pos;
+      if (Op::kLM) { t = e / L; pos = e - t * L; } else { pos = e / T; t = e - pos * T; }
+      const int o = Op::kLM ? blockIdx.x * T + t : blockIdx.y;
+      const int x = Op::kLM ? 0 : blockIdx.x * T + t;
+      const int pm = pos == 0 ? 0 : L - pos;
+      if (op.valid(o, x)) op.post(o, x, pos, tile[e], tile[tix<Op::kLM>(t, pm, T, L)], acc);
+    }
+    if (Op::kRed > 0) reduce_out<R, NR>(acc, op.part, op.pstride);
+    return;
+  }
   for (int e = threadIdx.x; e < T * L; e += kThreads) {
     int t, pos;
     if (Op::kLM) { t = e / L; pos = e - t * L; } else { pos = e / T; t = e - pos * T; }
@@ -306,79 +373,117 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
 }
 
 // ================================================================ ops
-// ---- ATKM (twofold-padded grid).  W1: [Nz][Ny][Mx], W2: [Nz][My][Mx].
-// x forward: lines o = z Ny + y; density formed on the fly, zero for x >= Nx.
+// ---- ATKM (twofold-padded grid, real-data form).  The density is real, so
+// the x transform of each padded line (length Mx = 2 Nx, upper half zero) is
+// taken as a complex FFT of length Nx of z_m = rho_{2m} + i rho_{2m+1} with the
+// exact post-twist X_k = (Z_k + conj Z_{Nx-k})/2 - (i/2) e^{-2 pi i k/Mx}
+// (Z_k - conj Z_{Nx-k}), k = 0..Nx (Hermitian symmetry gives the rest); the y
+// and z passes then run on the Nx + 1 half-spectrum columns only, and the
+// inverse x transform rebuilds the real output from that half (C2R).  With a
+// real density this equals the real part of the full complex convolution
+// once K is symmetrised on the padded Nyquist planes (see OpAtkmZ).
+// W1: [Nz][Ny][XS], W2: [Nz][My][XS], columns 0..Nx used.
 template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
-  const double* a; const double* b; cx<R>* W1; Cst<R> c;
-  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
-  __device__ cx<R> load(int o, int, int pos) const {
-    if (pos >= c.Nx) return czero<R>();
-    const size_t idx = (size_t)o * c.Nx + pos;
-    R v;
-    if (MODE == SRC_RHO) {
-      v = (R)a[idx];
-    } else if (MODE == SRC_PSI) {
+  static constexpr bool kMirror = true;
+  const double* a; const double* b; cx<R>* W1; const cx<R>* twM; Cst<R> c; int XS;
+  __device__ R dens(size_t idx) const {
+    if (MODE == SRC_RHO) return tor<R>(a[idx]);
+    if (MODE == SRC_PSI) {
       const cx<R> z = from64<R>(reinterpret_cast<const double2*>(a)[idx]);
-      v = z.x * z.x + z.y * z.y;
-    } else {
-      const cx<R> u = from64<R>(reinterpret_cast<const double2*>(a)[idx]);
-      const cx<R> w = from64<R>(reinterpret_cast<const double2*>(b)[idx]);
-      v = u.x * w.x + u.y * w.y;
+      return z.x * z.x + z.y * z.y;
     }
-    return mk<R>(v, (R)0);
+    const cx<R> u = from64<R>(reinterpret_cast<const double2*>(a)[idx]);
+    const cx<R> w = from64<R>(reinterpret_cast<const double2*>(b)[idx]);
+    return u.x * w.x + u.y * w.y;
+  }
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  // z_m = rho_{2m} + i rho_{2m+1}; zero for 2m >= Nx (the padding)
+  __device__ cx<R> load(int o, int, int m) const {
+    if (2 * m >= c.Nx) return czero<R>();
+    const size_t idx = (size_t)o * c.Nx + 2 * m;
+    return mk<R>(dens(idx), dens(idx + 1));
+  }
+  __device__ void post(int o, int, int k, cx<R> Zk, cx<R> Zm, R*) const {
+    const cx<R> Zc = mk<R>(Zm.x, -Zm.y);                 // conj Z_{Nx-k}
+    const cx<R> E = scl<R>(add<R>(Zk, Zc), (R)0.5);
+    const cx<R> D = scl<R>(sub<R>(Zk, Zc), (R)0.5);
+    const cx<R> w = twM[k];                               // e^{-2 pi i k / Mx}
+    const cx<R> wD = cmul<R>(w, D);
+    W1[(size_t)o * XS + k] = mk<R>(E.x + wD.y, E.y - wD.x);  // E - i w D
+    if (k == 0) W1[(size_t)o * XS + c.Nx] = mk<R>(Zk.x - Zk.y, (R)0);
   }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
-  __device__ void store(int o, int, int pos, cx<R> v, R*) const { W1[(size_t)o * c.Mx + pos] = v; }
+  __device__ void store(int, int, int, cx<R>, R*) const {}
 };
 
-// y forward: o = z, x = kx; rows y < Ny of W1, zero beyond.
+// y forward: o = z, x = kx in [0, Nx]; rows y < Ny of W1, zero beyond.
 template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
-  const cx<R>* W1; cx<R>* W2; Cst<R> c;
-  __device__ bool valid(int, int x) const { return x < c.Mx; }
+  const cx<R>* W1; cx<R>* W2; Cst<R> c; int XS;
+  __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const {
-    return pos < c.Ny ? W1[((size_t)o * c.Ny + pos) * c.Mx + x] : czero<R>();
+    return pos < c.Ny ? W1[((size_t)o * c.Ny + pos) * XS + x] : czero<R>();
   }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
-  __device__ void store(int o, int x, int pos, cx<R> v, R*) const { W2[((size_t)o * c.My + pos) * c.Mx + x] = v; }
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const { W2[((size_t)o * c.My + pos) * XS + x] = v; }
 };
 
-// z forward * K / (Mx My Mz) * inverse: o = ky, x = kx; rows z < Nz in and out.
+// z forward * K_sym / (Mx My Mz) * inverse: o = ky, x = kx in [0, Nx]; rows z < Nz.
+// K_sym = (K(k) + K(-k))/2 = -1 + 3 U0 (A^2 + B^2), A = sum of n_a nu_a over
+// axes whose index is not the padded Nyquist index, B over those that are.
 template <typename R> struct OpAtkmZ : OpBase<-1, true, 0, false> {
-  cx<R>* W2; const R* U0; Cst<R> c; R n0, n1, n2, invM;
-  __device__ bool valid(int, int x) const { return x < c.Mx; }
+  cx<R>* W2; const R* U0; Cst<R> c; R n0, n1, n2, invM; int XS;
+  __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const {
-    return pos < c.Nz ? W2[((size_t)pos * c.My + o) * c.Mx + x] : czero<R>();
+    return pos < c.Nz ? W2[((size_t)pos * c.My + o) * XS + x] : czero<R>();
   }
   __device__ void spectral(int o, int x, int k, cx<R>& v, R*) const {
-    const int kx = kfreq(x, c.Mx), ky = kfreq(o, c.My), kz = kfreq(k, c.Mz);
-    const R nd = n0 * ((R)kx * c.pkx) + n1 * ((R)ky * c.pky) + n2 * ((R)kz * c.pkz);
-    const R u = U0[((size_t)iabs(kz) * (c.Ny + 1) + iabs(ky)) * (c.Nx + 1) + iabs(kx)];
-    v = scl<R>(v, ((R)3 * nd * nd * u - (R)1) * invM);
+    const int ky = kfreq(o, c.My), kz = kfreq(k, c.Mz);
+    const int kx = x == c.Nx ? -c.Nx : x;  // signed frequency of the half-spectrum column
+    const R tx = n0 * ((R)kx * c.pkx), ty = n1 * ((R)ky * c.pky), tz = n2 * ((R)kz * c.pkz);
+    R A = (R)0, B = (R)0;
+    if (x == c.Nx) B += tx; else A += tx;
+    if (o == c.Ny) B += ty; else A += ty;
+    if (k == c.Nz) B += tz; else A += tz;
+    const R u = U0[((size_t)iabs(kz) * (c.Ny + 1) + iabs(ky)) * (c.Nx + 1) + x];
+    v = scl<R>(v, ((R)3 * u * (A * A + B * B) - (R)1) * invM);
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R*) const {
-    if (pos < c.Nz) W2[((size_t)pos * c.My + o) * c.Mx + x] = v;
+    if (pos < c.Nz) W2[((size_t)pos * c.My + o) * XS + x] = v;
   }
 };
 
-// y inverse: o = z, x = kx; output rows y < Ny into W1.
+// y inverse: o = z, x = kx in [0, Nx]; output rows y < Ny into W1.
 template <typename R> struct OpAtkmYI : OpBase<1, false, 0, false> {
-  const cx<R>* W2; cx<R>* W1; Cst<R> c;
-  __device__ bool valid(int, int x) const { return x < c.Mx; }
-  __device__ cx<R> load(int o, int x, int pos) const { return W2[((size_t)o * c.My + pos) * c.Mx + x]; }
+  const cx<R>* W2; cx<R>* W1; Cst<R> c; int XS;
+  __device__ bool valid(int, int x) const { return x <= c.Nx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return W2[((size_t)o * c.My + pos) * XS + x]; }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
   __device__ void store(int o, int x, int pos, cx<R> v, R*) const {
-    if (pos < c.Ny) W1[((size_t)o * c.Ny + pos) * c.Mx + x] = v;
+    if (pos < c.Ny) W1[((size_t)o * c.Ny + pos) * XS + x] = v;
   }
 };
 
-// x inverse: lines o; Phi = Re(.) for x < Nx.
+// x inverse (C2R): lines o; Z_k = (X_k + conj X_{Nx-k}) + i e^{2 pi i k/Mx}
+// (X_k - conj X_{Nx-k}), k < Nx, then an inverse FFT of length Nx gives
+// z_m = Phi_{2m} + i Phi_{2m+1}; kept for 2m < Nx (the crop).
 template <typename R> struct OpAtkmXI : OpBase<1, false, 0, true> {
-  const cx<R>* W1; double* phi; Cst<R> c;
+  const cx<R>* W1; double* phi; const cx<R>* twM; Cst<R> c; int XS;
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
-  __device__ cx<R> load(int o, int, int pos) const { return W1[(size_t)o * c.Mx + pos]; }
+  __device__ cx<R> load(int o, int, int k) const {
+    const cx<R>* row = W1 + (size_t)o * XS;
+    const cx<R> X = row[k], Xm = row[c.Nx - k];
+    const cx<R> Xc = mk<R>(Xm.x, -Xm.y);
+    const cx<R> S = add<R>(X, Xc), D = sub<R>(X, Xc);
+    const cx<R> w = twM[k];                               // conj gives e^{+2 pi i k / Mx}
+    const cx<R> wD = cmulc<R>(D, w);                      // D e^{+2 pi i k/Mx}
+    return mk<R>(S.x - wD.y, S.y + wD.x);                 // S + i wD
+  }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
-  __device__ void store(int o, int, int pos, cx<R> v, R*) const {
-    if (pos < c.Nx) phi[(size_t)o * c.Nx + pos] = (double)v.x;
+  __device__ void store(int o, int, int m, cx<R> v, R*) const {
+    if (2 * m < c.Nx) {
+      double2* dst = reinterpret_cast<double2*>(phi + (size_t)o * c.Nx + 2 * m);
+      *dst = make_double2(tod<R>(v.x), tod<R>(v.y));
+    }
   }
 };
 
@@ -445,11 +550,11 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
     const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
     const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
     const cx<R> fv = from64<R>(f[idx]), pv = from64<R>(phi[idx]);
-    const R Pd = (R)Phi[idx];
+    const R Pd = tor<R>(Phi[idx]);
     const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
     const cx<R> kin = add<R>(acc[idx], v);
     const R ox = kin.x + w * fv.x, oy = kin.y + w * fv.y;
-    Hf[idx] = make_double2((double)ox, (double)oy);
+    Hf[idx] = make_double2(tod<R>(ox), tod<R>(oy));
     if (RED) {
       const R f2 = fv.x * fv.x + fv.y * fv.y;
       a[1] += V * f2;
@@ -468,7 +573,7 @@ __device__ __forceinline__ R pv_rsqrt(const Cst<R>& c, const PhysR<R>& ph, R alp
   const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)y * c.hy, zc = -c.Lz + (R)z * c.hz;
   const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
   const cx<R> pv = from64<R>(p64);
-  const R Pd = (R)Pd64;
+  const R Pd = tor<R>(Pd64);
   const R den = alpha + V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + fabs(ph.lambda) * (Pd > (R)0 ? Pd : (R)0);
   return rsq<R>(den);
 }
@@ -478,7 +583,7 @@ template <typename R> struct OpPXF : OpBase<-1, false, 0, true> {
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
   __device__ cx<R> load(int o, int, int pos) const {
     const size_t idx = (size_t)o * c.Nx + pos;
-    const R w = pv_rsqrt<R>(c, ph, (R)*alpha, pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
+    const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
     return scl<R>(from64<R>(r[idx]), w);
   }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
@@ -501,7 +606,7 @@ template <typename R> struct OpPZ : OpBase<-1, true, 0, false> {
   __device__ void spectral(int o, int x, int k, cx<R>& v, R*) const {
     const R invN = (R)1 / ((R)c.Nx * (R)c.Ny * (R)c.Nz);
     const R nux = (R)kfreq(x, c.Nx) * c.kx, nuy = (R)kfreq(o, c.Ny) * c.ky, nuz = (R)kfreq(k, c.Nz) * c.kz;
-    v = scl<R>(v, invN / ((R)*alpha + (R)0.5 * (nux * nux + nuy * nuy + nuz * nuz)));
+    v = scl<R>(v, invN / (tor<R>(*alpha) + (R)0.5 * (nux * nux + nuy * nuy + nuz * nuz)));
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R*) const { Wk[((size_t)pos * c.Ny + o) * c.Nx + x] = v; }
 };
@@ -513,8 +618,8 @@ template <typename R> struct OpPXI : OpBase<1, false, 0, true> {
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
   __device__ void store(int o, int, int pos, cx<R> v, R*) const {
     const size_t idx = (size_t)o * c.Nx + pos;
-    const R w = pv_rsqrt<R>(c, ph, (R)*alpha, pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
-    Pr[idx] = make_double2((double)(w * v.x), (double)(w * v.y));
+    const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
+    Pr[idx] = make_double2(tod<R>(w * v.x), tod<R>(w * v.y));
   }
 };
 

@@ -41,49 +41,50 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
   const R* U0 = u0tab<R>(p);
   if (!W1 || !W2 || !U0) return cudaErrorInvalidValue;
   const Cst<R> c = make_cst<R>(g);
+  const cx<R>* twM = tw_table_host<R>(p->fM[0]);
   const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const double H1 = (double)g.Nz * g.Ny * g.Xh;  // half-spectrum elements of W1
   const double inb = mode == SRC_RHO ? 8.0 : (mode == SRC_PSI ? 16.0 : 32.0);
-  const double fx = (double)g.Nz * g.Ny * fftflops(g.Mx), fy = (double)g.Nz * g.Mx * fftflops(g.My);
-  const double fz = 2.0 * g.My * g.Mx * fftflops(g.Mz);
+  const double fx = (double)g.Nz * g.Ny * fftflops(g.Nx), fy = (double)g.Nz * g.Xh * fftflops(g.My);
+  const double fz = 2.0 * g.My * g.Xh * fftflops(g.Mz);
   const double u0b = (double)sizeof(R) * (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
   const long nl = (long)g.Nz * g.Ny;
-  // x forward
-  const PassGrid gx = pass_grid<R>(g.Mx, true, nl, 0, 0);
+  // x forward (real data: complex FFT of length Nx + post-twist)
+  const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
   const char* nx = nm<R>("atkm_x_fwd_f64", "atkm_x_fwd_f32");
   if (mode == SRC_RHO) {
-    OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = W1; op.c = c;
-    ATKM_RUN(nx, inb * N + 2 * N * s, fx, op, p->fM[0], gx);
+    OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
+    ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
   } else if (mode == SRC_PSI) {
-    OpAtkmXF<R, SRC_PSI> op; op.a = a; op.b = b; op.W1 = W1; op.c = c;
-    ATKM_RUN(nx, inb * N + 2 * N * s, fx, op, p->fM[0], gx);
+    OpAtkmXF<R, SRC_PSI> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
+    ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
   } else {
-    OpAtkmXF<R, SRC_PAIR> op; op.a = a; op.b = b; op.W1 = W1; op.c = c;
-    ATKM_RUN(nx, inb * N + 2 * N * s, fx, op, p->fM[0], gx);
+    OpAtkmXF<R, SRC_PAIR> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
+    ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
   }
-  // y forward
+  // y forward on the Nx + 1 half-spectrum columns
+  const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
   {
-    OpAtkmYF<R> op; op.W1 = W1; op.W2 = W2; op.c = c;
-    const PassGrid pg = pass_grid<R>(g.My, false, 0, g.Mx, g.Nz);
-    ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32"), 6 * N * s, fy, op, p->fM[1], pg);
+    OpAtkmYF<R> op; op.W1 = W1; op.W2 = W2; op.c = c; op.XS = g.XS;
+    ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32"), 3 * H1 * s, fy, op, p->fM[1], gy);
   }
-  // z forward * K * inverse
+  // z forward * K_sym * inverse
   {
-    OpAtkmZ<R> op; op.W2 = W2; op.U0 = U0; op.c = c;
+    OpAtkmZ<R> op; op.W2 = W2; op.U0 = U0; op.c = c; op.XS = g.XS;
     op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
     op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
-    const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Mx, g.My);
-    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32"), 8 * N * s + u0b, fz, op, p->fM[2], pg);
+    const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Xh, g.My);
+    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32"), 4 * H1 * s + u0b, fz, op, p->fM[2], pg);
   }
   // y inverse
   {
-    OpAtkmYI<R> op; op.W2 = W2; op.W1 = W1; op.c = c;
-    const PassGrid pg = pass_grid<R>(g.My, false, 0, g.Mx, g.Nz);
-    ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32"), 6 * N * s, fy, op, p->fM[1], pg);
+    OpAtkmYI<R> op; op.W2 = W2; op.W1 = W1; op.c = c; op.XS = g.XS;
+    ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32"), 3 * H1 * s, fy, op, p->fM[1], gy);
   }
-  // x inverse
+  // x inverse (C2R) + crop
   {
-    OpAtkmXI<R> op; op.W1 = W1; op.phi = phi; op.c = c;
-    ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32"), 2 * N * s + 8 * N, fx, op, p->fM[0], gx);
+    OpAtkmXI<R> op; op.W1 = W1; op.phi = phi; op.twM = twM; op.c = c; op.XS = g.XS;
+    ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32"), H1 * s + 8 * N, fx, op, p->fN[0], gx);
   }
   return cudaSuccess;
 }

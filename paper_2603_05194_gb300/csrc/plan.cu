@@ -330,6 +330,8 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   Geo& g = p->g;
   g.Nx = N[0]; g.Ny = N[1]; g.Nz = N[2];
   g.Mx = 2 * N[0]; g.My = 2 * N[1]; g.Mz = 2 * N[2];
+  g.Xh = N[0] + 1;
+  g.XS = (g.Xh + 15) / 16 * 16;
   g.Lx = L[0]; g.Ly = L[1]; g.Lz = L[2];
   g.hx = 2 * L[0] / N[0]; g.hy = 2 * L[1] / N[1]; g.hz = 2 * L[2] / N[2];
   p->hvol = g.hx * g.hy * g.hz;
@@ -407,12 +409,13 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan U0 precompute"));
   // ---- workspaces
   const size_t Nt = (size_t)g.Nx * g.Ny * g.Nz;
-  if ((e = dev_alloc(p, (void**)&p->W1, 2 * Nt * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
-  if ((e = dev_alloc(p, (void**)&p->W2, 4 * Nt * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
+  const size_t n_w1 = (size_t)g.Nz * g.Ny * g.XS, n_w2 = (size_t)g.Nz * g.My * g.XS;
+  if ((e = dev_alloc(p, (void**)&p->W1, n_w1 * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
+  if ((e = dev_alloc(p, (void**)&p->W2, n_w2 * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
   if ((e = dev_alloc(p, (void**)&p->T1, Nt * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
   if (flags & ATKM_PLAN_F32) {
-    if ((e = dev_alloc(p, (void**)&p->W1f, 2 * Nt * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
-    if ((e = dev_alloc(p, (void**)&p->W2f, 4 * Nt * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
+    if ((e = dev_alloc(p, (void**)&p->W1f, n_w1 * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
+    if ((e = dev_alloc(p, (void**)&p->W2f, n_w2 * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
     if ((e = dev_alloc(p, (void**)&p->T1f, Nt * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
     if ((e = dev_alloc(p, (void**)&p->U0f, n_oct * sizeof(float))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan U0f"));
     k_to_f32<<<(int)std::min<size_t>((n_oct + 255) / 256, 4096), 256, 0, st>>>(p->U0f, p->U0, n_oct);
