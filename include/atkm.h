@@ -202,6 +202,8 @@ typedef struct atkm_pcg_opts {
                            then output only); the iteration count, direction memory,
                            precision phase and energy carry over; max_iter counts
                            the iterations of this call                              */
+  int no_graphs;        /* != 0: launch every kernel directly instead of replaying the
+                           captured CUDA graph of an iteration (same results)       */
 } atkm_pcg_opts;
 
 /* One record per iteration n (values at phi_n; step fields describe n -> n+1). */
@@ -224,8 +226,12 @@ typedef struct atkm_result {
  * (Eq. (opt_step)) or t = 0.3, (iii) halving until the energy decreases.
  *   psi_inout  N complex: initial guess in, final state out (normalised on entry).
  *   out        host struct; out->log (host) receives per-iteration records.
- * Allocates the PCG vectors on first use (kept by the plan).  Synchronises
- * `stream` several times per iteration (the step decisions run on the host).
+ * Allocates the PCG vectors, a plan-owned stream and graph state on first use
+ * (kept by the plan).  The step decisions run in control kernels on the
+ * device; each iteration is a fixed kernel sequence captured once as a CUDA
+ * graph and replayed on the plan's stream, which is ordered after `stream`'s
+ * prior work on entry and before its later work on return.  The host
+ * synchronises once per iteration (stop rule, log) and once per halving.
  * Returns ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN or an
  * argument/CUDA error; out->status holds the same value.
  */

@@ -47,7 +47,7 @@ class Energy(C.Structure):
 class PcgOpts(C.Structure):
     _fields_ = [("tol_residual", C.c_double), ("tol_linf", C.c_double), ("max_iter", C.c_int),
                 ("max_halvings", C.c_int), ("precision_mode", C.c_int), ("switch_tol", C.c_double),
-                ("log_capacity", C.c_int), ("resume", C.c_int)]
+                ("log_capacity", C.c_int), ("resume", C.c_int), ("no_graphs", C.c_int)]
 
 
 class IterLog(C.Structure):
@@ -270,9 +270,9 @@ class Plan:
     # ---- Algorithm 1
     def pcg_ground_state(self, prm: Params, psi, tol_residual=1e-8, tol_linf=0.0, max_iter=10000,
                          max_halvings=20, precision=PRECISION_F64, switch_tol=1e-5, log_capacity=0,
-                         stream=None, check=True, resume=False) -> dict:
+                         stream=None, check=True, resume=False, graphs=True) -> dict:
         opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, log_capacity,
-                       1 if resume else 0)
+                       1 if resume else 0, 0 if graphs else 1)
         res = Result()
         logs = (IterLog * max(1, log_capacity))()
         res.log = C.cast(logs, C.POINTER(IterLog)) if log_capacity > 0 else C.POINTER(IterLog)()

@@ -1,21 +1,30 @@
-// Riemannian PCG (Algorithm 1, PCG-ATKM) on the device: deterministic FP64
-// reductions (fixed grid, fixed-order two-level sums), fused vector updates,
-// and the host-side step control of §2.3 (i)-(iii).
+// Riemannian PCG (Algorithm 1, PCG-ATKM) on the device.
 //
 // Per iteration n (phi = phi_n, Phi = Phi_n of the accepted previous trial):
 //   H phi (3 axis passes, fused energy sums) -> mu, r = H phi - mu phi, ||r||
 //   alpha -> P r (5 passes) -> PR+ scalars -> p, <H phi, p>, ||p||^2
+//   (Step 4 (i): if <H phi, p> >= 0, p is re-formed as J(-P r))
 //   H p, Phi' = U_dip * Re(conj(phi) p) -> curvature of Eq. (Energy_Expend)
 //   t (Eq. (opt_step) or 0.3) -> retraction (Eq. (retraction)), renormalise,
-//   Phi+ by ATKM, E(phi+) -> accept or halve.
+//   Phi+ by ATKM, E(phi+) -> accept, or halve t and retry (Step 4 (iii)).
+// All scalar decisions run in single-thread control kernels on a device
+// control block, and the vector kernels read their coefficients from it, so an
+// iteration is a fixed kernel sequence on ping-pong buffers: it is captured
+// once as a CUDA graph per (precision, buffer parity) and replayed, with one
+// host synchronisation per iteration (plus one per rare halving) to read the
+// control block for the stop rule and the log.
+//
 // The trial energy's quadratic part is formed from <A phi,phi>, <A phi,p>,
 // <A p,p> with A = -1/2[[Delta]] + V - Omega[[L_z]] (A is linear, so
 // <A phi+, phi+> expands exactly in cos/sin of the retraction); only the
-// quartic and dipolar terms need phi+ itself.
+// quartic and dipolar terms need phi+ itself.  Reductions are deterministic
+// (fixed grid, fixed-order two-level sums).
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
+#include <utility>
 #include <vector>
 
 #include "atkm_internal.cuh"
@@ -27,8 +36,29 @@ namespace {
 constexpr int kRedGrid = 1216;  // 8 CTAs per SM on 152 SMs
 constexpr int kRedThreads = 256;
 
-// ---------------------------------------------------------- reductions
-__global__ void k_finalize(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+// ------------------------------------------------------------ control block
+struct Ctl {
+  // constants of the solve
+  double hv, beta, lam, tolE_eps;
+  // state carried between iterations
+  double E, den_prev;
+  int have_E, have_prev, force_sd, pad0;
+  // loop top of the current iteration
+  double kin, rot, pot, f4, dip, mu, norm2, res, alpha;
+  // direction
+  double b, den, beta_cg, cp0, cp1, cp2, pn2, d1;
+  int use_cg, reset, redo, nan;
+  // step
+  double Hpp, S1, S2, S3, curv, t0, t, pn, Aphiphi, Aphip, App, tolE;
+  double cr, sr, nrm2, inv, En, linf, bestE, best_t;
+  int accepted, nh, forced, pad1;
+  double inv0;  // normalisation of psi_0
+};
+
+// ------------------------------------------------------------ reductions
+__global__ void k_finalize(const double* __restrict__ part, int nblocks, double* __restrict__ out,
+                           const int* __restrict__ pred) {
+  if (pred && !*pred) return;
   __shared__ double sh[kRedThreads];
   const int s = blockIdx.x;
   double acc = 0.0;
@@ -79,18 +109,27 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(DotPairs dp, size_t N, dou
   block_reduce_store<kMaxDots>(acc, part, gridDim.x, blockIdx.x);
 }
 
+// A coefficient m * (*p) (p may be null: then m).
+struct Coef {
+  const double* p;
+  double m;
+};
+__device__ __forceinline__ double cval(const Coef& c) { return c.p ? c.m * *c.p : c.m; }
+
 // out = c0 v0 + c1 v1 + c2 v2 (null vectors skipped); sums |out|^2 and
-// Re(w conj(out)) when w is given.
+// Re(w conj(out)) when w is given.  Skipped entirely when *pred == 0.
 __global__ void __launch_bounds__(kRedThreads)
-k_lincomb(double2* __restrict__ out, const double2* __restrict__ v0, double c0, const double2* __restrict__ v1,
-          double c1, const double2* __restrict__ v2, double c2, const double2* __restrict__ w, size_t N,
-          double* __restrict__ part) {
+k_lincomb(double2* __restrict__ out, const double2* __restrict__ v0, Coef c0, const double2* __restrict__ v1,
+          Coef c1, const double2* __restrict__ v2, Coef c2, const double2* __restrict__ w, size_t N,
+          double* __restrict__ part, const int* __restrict__ pred) {
+  if (pred && !*pred) return;
+  const double a0 = cval(c0), a1 = cval(c1), a2 = cval(c2);
   double acc[2] = {0.0, 0.0};
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
     double2 o = make_double2(0.0, 0.0);
-    if (v0) { const double2 a = v0[j]; o.x += c0 * a.x; o.y += c0 * a.y; }
-    if (v1) { const double2 a = v1[j]; o.x += c1 * a.x; o.y += c1 * a.y; }
-    if (v2) { const double2 a = v2[j]; o.x += c2 * a.x; o.y += c2 * a.y; }
+    if (v0) { const double2 a = v0[j]; o.x += a0 * a.x; o.y += a0 * a.y; }
+    if (v1) { const double2 a = v1[j]; o.x += a1 * a.x; o.y += a1 * a.y; }
+    if (v2) { const double2 a = v2[j]; o.x += a2 * a.x; o.y += a2 * a.y; }
     out[j] = o;
     acc[0] += o.x * o.x + o.y * o.y;
     if (w) { const double2 b = w[j]; acc[1] += b.x * o.x + b.y * o.y; }
@@ -98,11 +137,12 @@ k_lincomb(double2* __restrict__ out, const double2* __restrict__ v0, double c0, 
   block_reduce_store<2>(acc, part, gridDim.x, blockIdx.x);
 }
 
-// phi+ *= inv; block max of |phi+ - phi|.
+// phi+ *= *inv; block max of |phi+ - phi|.
 __global__ void __launch_bounds__(kRedThreads)
-k_scale_linf(double2* __restrict__ phin, const double2* __restrict__ phi, double inv, size_t N,
+k_scale_linf(double2* __restrict__ phin, const double2* __restrict__ phi, const double* __restrict__ invp, size_t N,
              double* __restrict__ part) {
   __shared__ double sh[kRedThreads];
+  const double inv = *invp;
   double m = 0.0;
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
     double2 a = phin[j];
@@ -161,96 +201,7 @@ int red_grid(size_t N) {
   return (int)b;
 }
 
-}  // namespace
-
-cudaError_t launch_finalize(atkm_plan* p, int nslots, int nblocks, int dst_slot, cudaStream_t st) {
-  k_finalize<<<nslots, kRedThreads, 0, st>>>(p->partials, nblocks, p->scal + dst_slot);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-// ------------------------------------------------------------- PCG state
-struct PcgBuffers {
-  size_t N = 0;
-  double2 *phi = nullptr, *Hphi = nullptr, *r = nullptr, *Pr = nullptr, *p = nullptr, *pprev = nullptr,
-          *rprev = nullptr, *Hp = nullptr, *phin = nullptr;
-  double *Phi = nullptr, *Phi1 = nullptr, *Phin = nullptr;
-  // scalar state carried between calls (resume)
-  bool valid = false, f32 = false, have_prev = false, force_sd = true;
-  int n = 0, caps = 0;
-  double E = 0.0, den_prev = 0.0, linf = INFINITY;
-};
-
-void pcg_free(atkm_plan* p) {
-  if (!p->pcg) return;
-  PcgBuffers* b = p->pcg;
-  void* ptrs[] = {b->phi, b->Hphi, b->r, b->Pr, b->p, b->pprev, b->rprev, b->Hp, b->phin, b->Phi, b->Phi1, b->Phin};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
-  delete b;
-  p->pcg = nullptr;
-}
-
-static cudaError_t pcg_alloc(atkm_plan* p) {
-  if (p->pcg) return cudaSuccess;
-  PcgBuffers* b = new PcgBuffers();
-  p->pcg = b;
-  const size_t N = (size_t)p->g.Nx * p->g.Ny * p->g.Nz;
-  b->N = N;
-  double2** cv[] = {&b->phi, &b->Hphi, &b->r, &b->Pr, &b->p, &b->pprev, &b->rprev, &b->Hp, &b->phin};
-  for (double2** q : cv) {
-    cudaError_t e = dev_alloc(p, (void**)q, N * sizeof(double2));
-    if (e != cudaSuccess) { pcg_free(p); return e; }
-  }
-  double** rv[] = {&b->Phi, &b->Phi1, &b->Phin};
-  for (double** q : rv) {
-    cudaError_t e = dev_alloc(p, (void**)q, N * sizeof(double));
-    if (e != cudaSuccess) { pcg_free(p); return e; }
-  }
-  // the previous-iteration vectors are read (and ignored) before the first
-  // step; give them defined contents
-  cudaError_t e = cudaMemset(b->pprev, 0, N * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMemset(b->rprev, 0, N * sizeof(double2));
-  if (e != cudaSuccess) pcg_free(p);
-  return e;
-}
-
-// Small helper bundling plan, stream and the scalar read-back.
-struct Dev {
-  atkm_plan* p;
-  cudaStream_t st;
-  size_t N;
-  cudaError_t err = cudaSuccess;
-
-  void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
-  // Launch k_dots for the given pairs into scal[dst..dst+n).
-  void dots(std::initializer_list<std::pair<const double2*, const double2*>> pairs, int dst) {
-    DotPairs dp;
-    memset(&dp, 0, sizeof(dp));
-    for (auto& pr : pairs) { dp.u[dp.n] = pr.first; dp.v[dp.n] = pr.second; ++dp.n; }
-    const int G = red_grid(N);
-    k_dots<<<G, kRedThreads, 0, st>>>(dp, N, p->partials);
-    count_launches(1);
-    chk(cudaGetLastError());
-    chk(launch_finalize(p, dp.n, G, dst, st));
-  }
-  void lincomb(double2* out, const double2* v0, double c0, const double2* v1, double c1, const double2* v2,
-               double c2, const double2* w, int dst) {
-    const int G = red_grid(N);
-    k_lincomb<<<G, kRedThreads, 0, st>>>(out, v0, c0, v1, c1, v2, c2, w, N, p->partials);
-    count_launches(1);
-    chk(cudaGetLastError());
-    chk(launch_finalize(p, 2, G, dst, st));
-  }
-  // Copies scal[lo..hi) to the pinned mirror and waits.
-  void fetch(int lo, int hi) {
-    chk(cudaMemcpyAsync(p->scal_host + lo, p->scal + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    chk(cudaStreamSynchronize(st));
-  }
-  double h(int i) const { return p->scal_host[i]; }
-};
-
-// Slots used by the driver.
+// Slots of plan->scal used by the driver.
 enum {
   S_H = SC_RED,          // 10 slots of the H phi reductions
   S_R = SC_RED + 10,     // |r|^2 (+ unused)
@@ -263,20 +214,393 @@ enum {
   S_N = SC_RED + 31      // |psi0|^2
 };
 
-struct Parts {
-  double kin, rot, pot, f4, dip, mu, norm2;
+// ------------------------------------------------------------ control kernels
+__device__ __forceinline__ bool fin(double v) { return isfinite(v); }
+
+__global__ void k_c_init(Ctl* c, const double* s) {
+  const double n0 = sqrt(c->hv * s[S_N]);
+  c->nan = !(n0 > 0.0) || !fin(n0);
+  c->inv0 = c->nan ? 0.0 : 1.0 / n0;
+}
+
+// loop top: energy terms of phi, mu, alpha (Step 2 and the shift of §2.3)
+__global__ void k_c_parts(Ctl* c, const double* s) {
+  const double hv = c->hv;
+  c->kin = hv * (s[S_H + 0] + s[S_H + 2] + s[S_H + 4]);
+  c->rot = hv * (s[S_H + 1] + s[S_H + 3]);
+  c->pot = hv * s[S_H + 5];
+  c->f4 = hv * s[S_H + 6];
+  c->dip = hv * s[S_H + 7];
+  c->mu = hv * s[S_H + 8];
+  c->norm2 = hv * s[S_H + 9];
+  if (!c->have_E) {
+    c->E = c->kin + c->rot + c->pot + 0.5 * c->beta * c->f4 + 0.5 * c->lam * c->dip;
+    c->have_E = 1;
+  }
+  c->alpha = c->kin + c->pot + c->beta * c->f4 + fabs(c->lam * c->dip);
+}
+
+__global__ void k_c_res(Ctl* c, const double* s) {
+  c->res = sqrt(c->hv * s[S_R]);
+  c->nan = !fin(c->E) || !fin(c->res) || !fin(c->mu);
+}
+
+// Step 3: PR+ coefficients, p = cp0 P r + cp1 p_prev + cp2 phi
+__global__ void k_c_dir(Ctl* c, const double* s) {
+  const double hv = c->hv;
+  const double b = hv * s[S_D + 0], rPr = hv * s[S_D + 1], rphi = hv * s[S_D + 2];
+  const double rpPr = hv * s[S_D + 3], a = hv * s[S_D + 4], cc = hv * s[S_D + 5], nphi = hv * s[S_D + 6];
+  c->b = b;
+  c->den = rPr - b * rphi;  // <r, J(P r)>
+  c->use_cg = c->have_prev && !c->force_sd;
+  c->reset = 0;
+  if (c->use_cg) {
+    const double jrj = rpPr - 2.0 * a * b + a * b * nphi;  // <J(r_prev), J(P r)>
+    const double bcg = fmax((c->den - jrj) / c->den_prev, 0.0);
+    c->beta_cg = bcg;
+    c->cp0 = -1.0; c->cp1 = bcg; c->cp2 = b - bcg * cc;
+  } else {
+    c->beta_cg = 0.0;
+    c->cp0 = -1.0; c->cp1 = 0.0; c->cp2 = b;
+  }
+}
+
+// Step 4 (i): keep p if <H phi, p> < 0, otherwise re-form it as J(-P r)
+__global__ void k_c_reset(Ctl* c, const double* s) {
+  c->pn2 = c->hv * s[S_P];
+  c->d1 = c->hv * s[S_P + 1];
+  c->redo = 0;
+  if (c->d1 >= 0.0) {
+    c->reset = 1;
+    c->beta_cg = 0.0;
+    if (c->use_cg) {
+      c->cp0 = -1.0; c->cp1 = 0.0; c->cp2 = c->b;
+      c->redo = 1;
+    }
+  }
+}
+
+__global__ void k_c_reset2(Ctl* c, const double* s) {
+  if (!c->redo) return;
+  c->pn2 = c->hv * s[S_P];
+  c->d1 = c->hv * s[S_P + 1];
+}
+
+// Step 4 (ii): quadratic model, initial t, first retraction coefficients
+__global__ void k_c_step(Ctl* c, const double* s) {
+  const double hv = c->hv;
+  c->Hpp = hv * s[S_C]; c->S1 = hv * s[S_C + 1]; c->S2 = hv * s[S_C + 2]; c->S3 = hv * s[S_C + 3];
+  c->curv = c->Hpp + 2.0 * c->S1 - c->mu * c->pn2;
+  c->t = c->curv > 0.0 ? -c->d1 / c->curv : 0.3;
+  c->t0 = c->t;
+  c->pn = sqrt(c->pn2);
+  c->Aphiphi = c->kin + c->rot + c->pot;
+  c->Aphip = c->d1 - c->S2;
+  c->App = c->Hpp - c->S3;
+  c->tolE = c->tolE_eps * fabs(c->E);
+  c->nh = 0;
+  c->forced = 0;
+  c->bestE = INFINITY;
+  c->best_t = c->t;
+  c->cr = cos(c->t * c->pn);
+  c->sr = sin(c->t * c->pn) / c->pn;
+}
+
+__global__ void k_c_norm(Ctl* c, const double* s) {
+  c->nrm2 = c->hv * s[S_T];
+  c->inv = 1.0 / sqrt(c->nrm2);
+}
+
+// Step 4 (iii): trial energy and the acceptance test
+__global__ void k_c_accept(Ctl* c, const double* s) {
+  const double quad = (c->cr * c->cr * c->Aphiphi + 2.0 * c->cr * c->sr * c->Aphip + c->sr * c->sr * c->App) / c->nrm2;
+  c->En = quad + 0.5 * c->beta * c->hv * s[S_Q] + 0.5 * c->lam * c->hv * s[S_Q + 1];
+  c->linf = s[S_L];
+  c->accepted = fin(c->En) && (c->En <= c->E + c->tolE);
+  if (!c->accepted && c->En < c->bestE) {
+    c->bestE = c->En;
+    c->best_t = c->t;
+  }
+}
+
+// Next trial: halve t, or (mode 1) take the lowest-energy trial seen.
+__global__ void k_c_halve(Ctl* c, int mode) {
+  if (mode == 0) {
+    c->t *= 0.5;
+    c->nh += 1;
+  } else {
+    c->t = c->best_t;
+    c->forced = 1;
+  }
+  c->cr = cos(c->t * c->pn);
+  c->sr = sin(c->t * c->pn) / c->pn;
+}
+
+// End of an iteration: the trial becomes phi_{n+1}.
+__global__ void k_c_end(Ctl* c) {
+  c->den_prev = c->den;
+  c->have_prev = 1;
+  c->E = c->En;
+  c->force_sd = c->forced;
+}
+
+// Host-driven state changes (precision hand-over, start of a solve).
+__global__ void k_c_reset_state(Ctl* c, int have_E, int force_sd, int clear_prev) {
+  c->have_E = have_E;
+  c->force_sd = force_sd;
+  if (clear_prev) c->have_prev = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(atkm_plan* p, int nslots, int nblocks, int dst_slot, cudaStream_t st) {
+  k_finalize<<<nslots, kRedThreads, 0, st>>>(p->partials, nblocks, p->scal + dst_slot, nullptr);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- PCG state
+struct PcgBuffers {
+  size_t N = 0;
+  double2* phi[2] = {nullptr, nullptr};  // ping-pong: phi_n / trial phi+
+  double2* r[2] = {nullptr, nullptr};    // r_n / r_{n-1}
+  double2* p[2] = {nullptr, nullptr};    // p_n / p_{n-1}
+  double* Phi[2] = {nullptr, nullptr};   // Phi_n / trial Phi+
+  double2 *Hphi = nullptr, *Pr = nullptr, *Hp = nullptr;
+  double* Phi1 = nullptr;
+  Ctl* ctl = nullptr;        // device
+  Ctl* ctl_h = nullptr;      // pinned host mirror
+  cudaStream_t st = nullptr; // plan-owned stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // graphs: [f32][parity][kind: 0 iteration, 1 halve+trial, 2 best+trial]
+  cudaGraphExec_t gx[2][2][3] = {};
+  int gnodes[2][2][3] = {};
+  bool seen[2][2][3] = {};
+  bool graphs_ok = true;
+  Phys gphys{};
+  bool gphys_set = false;
+  // resume state (host side)
+  bool valid = false, f32 = false;
+  int parity = 0, n = 0, caps = 0;
+  double linf = INFINITY;
 };
 
-static Parts read_parts(const Dev& d, double hvol) {
-  Parts q;
-  q.kin = hvol * (d.h(S_H + 0) + d.h(S_H + 2) + d.h(S_H + 4));
-  q.rot = hvol * (d.h(S_H + 1) + d.h(S_H + 3));
-  q.pot = hvol * d.h(S_H + 5);
-  q.f4 = hvol * d.h(S_H + 6);
-  q.dip = hvol * d.h(S_H + 7);
-  q.mu = hvol * d.h(S_H + 8);
-  q.norm2 = hvol * d.h(S_H + 9);
-  return q;
+static void destroy_graphs(PcgBuffers* b) {
+  for (auto& a : b->gx)
+    for (auto& c : a)
+      for (auto& g : c)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  memset(b->seen, 0, sizeof(b->seen));
+  memset(b->gnodes, 0, sizeof(b->gnodes));
+}
+
+void pcg_free(atkm_plan* p) {
+  if (!p->pcg) return;
+  PcgBuffers* b = p->pcg;
+  destroy_graphs(b);
+  void* ptrs[] = {b->phi[0], b->phi[1], b->r[0], b->r[1], b->p[0], b->p[1], b->Phi[0], b->Phi[1],
+                  b->Hphi, b->Pr, b->Hp, b->Phi1, b->ctl};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (b->ctl_h) cudaFreeHost(b->ctl_h);
+  if (b->st) cudaStreamDestroy(b->st);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  delete b;
+  p->pcg = nullptr;
+}
+
+static cudaError_t pcg_alloc(atkm_plan* p) {
+  if (p->pcg) return cudaSuccess;
+  PcgBuffers* b = new PcgBuffers();
+  p->pcg = b;
+  const size_t N = (size_t)p->g.Nx * p->g.Ny * p->g.Nz;
+  b->N = N;
+  double2** cv[] = {&b->phi[0], &b->phi[1], &b->r[0], &b->r[1], &b->p[0], &b->p[1], &b->Hphi, &b->Pr, &b->Hp};
+  cudaError_t e = cudaSuccess;
+  for (double2** q : cv)
+    if (e == cudaSuccess) e = dev_alloc(p, (void**)q, N * sizeof(double2));
+  double** rv[] = {&b->Phi[0], &b->Phi[1], &b->Phi1};
+  for (double** q : rv)
+    if (e == cudaSuccess) e = dev_alloc(p, (void**)q, N * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc(p, (void**)&b->ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->ctl_h, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  // previous-iteration vectors are read (and ignored) before the first step
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMemset(b->r[i], 0, N * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemset(b->p[i], 0, N * sizeof(double2));
+  }
+  if (e == cudaSuccess) e = cudaMemset(b->ctl, 0, sizeof(Ctl));
+  if (e != cudaSuccess) pcg_free(p);
+  return e;
+}
+
+// Enqueues the kernels of one PCG phase on the plan stream.
+struct Seq {
+  atkm_plan* p;
+  PcgBuffers& B;
+  Phys ph;
+  bool f32;
+  int q;  // buffer parity: phi = B.phi[q], trial into B.phi[q ^ 1]
+  cudaError_t err = cudaSuccess;
+  Ctl* c() const { return B.ctl; }
+  const double* s() const { return p->scal; }
+  cudaStream_t st() const { return B.st; }
+  void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
+  int G() const { return red_grid(B.N); }
+
+  void dots(std::initializer_list<std::pair<const double2*, const double2*>> pairs, int dst) {
+    DotPairs dp;
+    memset(&dp, 0, sizeof(dp));
+    for (auto& pr : pairs) { dp.u[dp.n] = pr.first; dp.v[dp.n] = pr.second; ++dp.n; }
+    k_dots<<<G(), kRedThreads, 0, st()>>>(dp, B.N, p->partials);
+    count_launches(1);
+    chk(cudaGetLastError());
+    chk(launch_finalize(p, dp.n, G(), dst, st()));
+  }
+  void lincomb(double2* out, const double2* v0, Coef c0, const double2* v1, Coef c1, const double2* v2, Coef c2,
+               const double2* w, int dst, const int* pred = nullptr) {
+    k_lincomb<<<G(), kRedThreads, 0, st()>>>(out, v0, c0, v1, c1, v2, c2, w, B.N, p->partials, pred);
+    k_finalize<<<2, kRedThreads, 0, st()>>>(p->partials, G(), p->scal + dst, pred);
+    count_launches(2);
+    chk(cudaGetLastError());
+  }
+  void atkm(int mode, const double* a, const double* b, double* o) {
+    chk(f32 ? launch_atkm<float>(p, mode, a, b, o, st()) : launch_atkm<double>(p, mode, a, b, o, st()));
+  }
+  void hop(const double2* f, double2* o, int red) {
+    const double* fp = reinterpret_cast<const double*>(f);
+    const double* pp = reinterpret_cast<const double*>(B.phi[q]);
+    double* op = reinterpret_cast<double*>(o);
+    chk(f32 ? launch_H<float>(p, ph, fp, pp, B.Phi[q], op, red, st())
+            : launch_H<double>(p, ph, fp, pp, B.Phi[q], op, red, st()));
+  }
+  template <typename K, typename... A> void ctl1(K kernel, A... args) {
+    kernel<<<1, 1, 0, st()>>>(args...);
+    count_launches(1);
+    chk(cudaGetLastError());
+  }
+
+  // Step 2 only (loop top): H phi, parts, r, ||r||.
+  void top() {
+    hop(B.phi[q], B.Hphi, S_H);
+    ctl1(k_c_parts, c(), s());
+    lincomb(B.r[q], B.Hphi, Coef{nullptr, 1.0}, B.phi[q], Coef{&c()->mu, -1.0}, nullptr, Coef{nullptr, 0.0}, nullptr,
+            S_R);
+    ctl1(k_c_res, c(), s());
+  }
+  // One trial of Step 4 (iii) with the current retraction coefficients.
+  void trial() {
+    double2* phin = B.phi[q ^ 1];
+    lincomb(phin, B.phi[q], Coef{&c()->cr, 1.0}, B.p[q], Coef{&c()->sr, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr,
+            S_T);
+    ctl1(k_c_norm, c(), s());
+    k_scale_linf<<<G(), kRedThreads, 0, st()>>>(phin, B.phi[q], &c()->inv, B.N, p->partials);
+    k_finalize_max<<<1, kRedThreads, 0, st()>>>(p->partials, G(), p->scal + S_L);
+    count_launches(2);
+    chk(cudaGetLastError());
+    atkm(SRC_PSI, reinterpret_cast<const double*>(phin), nullptr, B.Phi[q ^ 1]);
+    k_quartic_sums<<<G(), kRedThreads, 0, st()>>>(phin, B.Phi[q ^ 1], B.N, p->partials);
+    count_launches(1);
+    chk(cudaGetLastError());
+    chk(launch_finalize(p, 2, G(), S_Q, st()));
+    ctl1(k_c_accept, c(), s());
+  }
+  cudaError_t precond() {
+    const double* r = reinterpret_cast<const double*>(B.r[q]);
+    const double* phi = reinterpret_cast<const double*>(B.phi[q]);
+    double* Pr = reinterpret_cast<double*>(B.Pr);
+    return f32 ? launch_precond<float>(p, ph, &c()->alpha, r, phi, B.Phi[q], Pr, st())
+               : launch_precond<double>(p, ph, &c()->alpha, r, phi, B.Phi[q], Pr, st());
+  }
+  // A whole iteration: Steps 2-4 up to the first trial.
+  void iteration() {
+    top();
+    chk(precond());
+    dots({{B.Pr, B.phi[q]}, {B.r[q], B.Pr}, {B.r[q], B.phi[q]}, {B.r[q ^ 1], B.Pr}, {B.r[q ^ 1], B.phi[q]},
+          {B.p[q ^ 1], B.phi[q]}, {B.phi[q], B.phi[q]}},
+         S_D);
+    ctl1(k_c_dir, c(), s());
+    lincomb(B.p[q], B.Pr, Coef{&c()->cp0, 1.0}, B.p[q ^ 1], Coef{&c()->cp1, 1.0}, B.phi[q], Coef{&c()->cp2, 1.0},
+            B.Hphi, S_P);
+    ctl1(k_c_reset, c(), s());
+    lincomb(B.p[q], B.Pr, Coef{nullptr, -1.0}, B.phi[q], Coef{&c()->b, 1.0}, nullptr, Coef{nullptr, 0.0}, B.Hphi, S_P,
+            &c()->redo);
+    ctl1(k_c_reset2, c(), s());
+    hop(B.p[q], B.Hp, -1);
+    atkm(SRC_PAIR, reinterpret_cast<const double*>(B.phi[q]), reinterpret_cast<const double*>(B.p[q]), B.Phi1);
+    dots({{B.Hp, B.p[q]}}, S_C);
+    k_curv_sums<<<G(), kRedThreads, 0, st()>>>(B.phi[q], B.p[q], B.Phi[q], B.Phi1, ph.beta, ph.lambda, B.N,
+                                                p->partials);
+    count_launches(1);
+    chk(cudaGetLastError());
+    chk(launch_finalize(p, 3, G(), S_C + 1, st()));
+    ctl1(k_c_step, c(), s());
+    trial();
+  }
+  void run(int kind) {
+    if (kind == 0) {
+      iteration();
+    } else {
+      ctl1(k_c_halve, c(), kind == 1 ? 0 : 1);
+      trial();
+    }
+  }
+};
+
+// Runs a phase through its CUDA graph (captured on the second use) or eagerly.
+static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
+  PcgBuffers& B = S.B;
+  const int fi = S.f32 ? 1 : 0;
+  if (!use_graphs || !B.graphs_ok) {
+    S.run(kind);
+    return S.err;
+  }
+  cudaGraphExec_t& gx = B.gx[fi][S.q][kind];
+  if (gx) {
+    count_launches(B.gnodes[fi][S.q][kind]);
+    return cudaGraphLaunch(gx, B.st);
+  }
+  if (!B.seen[fi][S.q][kind]) {  // first use: run eagerly (prepares kernel attributes)
+    B.seen[fi][S.q][kind] = true;
+    S.run(kind);
+    return S.err;
+  }
+  const unsigned long long c0 = atkm_launch_count();
+  if (cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    B.graphs_ok = false;
+    S.run(kind);
+    return S.err;
+  }
+  S.run(kind);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(B.st, &g);
+  const int nodes = (int)(atkm_launch_count() - c0);
+  count_launches(-nodes);  // recorded into the graph, not executed
+  if (S.err != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    B.graphs_ok = false;
+    S.err = cudaSuccess;
+    S.run(kind);
+    return S.err;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    gx = nullptr;
+    cudaGetLastError();
+    B.graphs_ok = false;
+    S.run(kind);
+    return S.err;
+  }
+  B.gnodes[fi][S.q][kind] = nodes;
+  count_launches(nodes);
+  return cudaGraphLaunch(gx, B.st);
 }
 
 }  // namespace atkm
@@ -288,21 +612,24 @@ extern "C" {
 int atkm_energy_parts(atkm_plan* plan, const atkm_params* prm, const double* phi, const double* Phi,
                       atkm_energy* out, void* stream) {
   if (!plan || !prm || !phi || !Phi || !out) return fail(plan, ATKM_ERR_ARG, "atkm_energy_parts: NULL argument");
-  Dev d{plan, (cudaStream_t)stream, (size_t)plan->g.Nx * plan->g.Ny * plan->g.Nz};
+  cudaStream_t st = (cudaStream_t)stream;
   // W1 holds at least N complex values and is free outside the ATKM passes.
-  d.chk(launch_H<double>(plan, make_phys(prm), phi, phi, Phi, reinterpret_cast<double*>(plan->W1), S_H, d.st));
-  d.fetch(S_H, S_H + 10);
-  if (d.err != cudaSuccess) return cuda_fail(plan, d.err, "atkm_energy_parts");
-  const Parts q = read_parts(d, plan->hvol);
-  out->E_kin = q.kin;
-  out->E_rot = q.rot;
-  out->E_pot = q.pot;
-  out->E_int = 0.5 * prm->beta * q.f4;
-  out->E_dip = 0.5 * prm->lambda * q.dip;
+  cudaError_t e = launch_H<double>(plan, make_phys(prm), phi, phi, Phi, reinterpret_cast<double*>(plan->W1), S_H, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->scal_host + S_H, plan->scal + S_H, 10 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(plan, e, "atkm_energy_parts");
+  const double hv = plan->hvol;
+  const double* h = plan->scal_host;
+  out->E_kin = hv * (h[S_H + 0] + h[S_H + 2] + h[S_H + 4]);
+  out->E_rot = hv * (h[S_H + 1] + h[S_H + 3]);
+  out->E_pot = hv * h[S_H + 5];
+  out->E_int = 0.5 * prm->beta * hv * h[S_H + 6];
+  out->E_dip = 0.5 * prm->lambda * hv * h[S_H + 7];
   out->E = out->E_kin + out->E_rot + out->E_pot + out->E_int + out->E_dip;
-  out->mu = q.mu;
+  out->mu = hv * h[S_H + 8];
   out->virial = 2 * out->E_kin - 2 * out->E_pot + 3 * out->E_int + 3 * out->E_dip;
-  out->norm2 = q.norm2;
+  out->norm2 = hv * h[S_H + 9];
   return ATKM_OK;
 }
 
@@ -335,258 +662,169 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
   cudaError_t ae = pcg_alloc(plan);
   if (ae != cudaSuccess) return cuda_fail(plan, ae, "pcg_ground_state: allocation");
   PcgBuffers& B = *plan->pcg;
-  Dev d{plan, (cudaStream_t)stream, B.N};
-  const double hv = plan->hvol;
+  cudaStream_t caller = (cudaStream_t)stream;
   const Phys ph = make_phys(prm);
-  const double beta = prm->beta, lam = prm->lambda;
+  if (B.gphys_set && memcmp(&B.gphys, &ph, sizeof(Phys)) != 0) destroy_graphs(&B);
+  B.gphys = ph;
+  B.gphys_set = true;
+  const bool use_graphs = (plan->prof == nullptr) && !opts->no_graphs;
   const double eps64 = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
+  cudaError_t err = cudaSuccess;
+  auto chk = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; };
+  // order after the caller's prior work
+  chk(cudaEventRecord(B.ev_in, caller));
+  chk(cudaStreamWaitEvent(B.st, B.ev_in, 0));
 
-  // Select precision for the spectral operators.
   bool f32 = mixed;
-  auto ATKM = [&](int mode, const double* a, const double* b, double* o) {
-    d.chk(f32 ? launch_atkm<float>(plan, mode, a, b, o, d.st) : launch_atkm<double>(plan, mode, a, b, o, d.st));
-  };
-  auto HOP = [&](const double* f, double* o, int red) {
-    d.chk(f32 ? launch_H<float>(plan, ph, reinterpret_cast<const double*>(f), reinterpret_cast<const double*>(B.phi),
-                                B.Phi, o, red, d.st)
-              : launch_H<double>(plan, ph, reinterpret_cast<const double*>(f), reinterpret_cast<const double*>(B.phi),
-                                 B.Phi, o, red, d.st));
-  };
-  auto PREC = [&]() {
-    d.chk(f32 ? launch_precond<float>(plan, ph, plan->scal + SC_ALPHA, (double*)B.r, (double*)B.phi, B.Phi,
-                                      (double*)B.Pr, d.st)
-              : launch_precond<double>(plan, ph, plan->scal + SC_ALPHA, (double*)B.r, (double*)B.phi, B.Phi,
-                                       (double*)B.Pr, d.st));
-  };
-  auto fail_cuda = [&]() {
-    out->status = ATKM_ERR_CUDA;
-    return cuda_fail(plan, d.err, "pcg_ground_state");
-  };
-
-  double E = 0.0, den_prev = 0.0, linf = INFINITY;
-  bool have_E = false, force_sd = true, have_prev = false;
-  int caps = 0, n = 0, status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0;
-  int n_start = 0;
+  int q = 0, n = 0, n_start = 0, caps = 0;
+  double linf = INFINITY;
   double f32_best = INFINITY;
   int f32_best_n = 0;
+  Ctl& H = *B.ctl_h;
+  auto fetch = [&]() {
+    chk(cudaMemcpyAsync(B.ctl_h, B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, B.st));
+    chk(cudaStreamSynchronize(B.st));
+  };
+  auto set_scalar = [&](double* dst, double v) {
+    k_set_scalar<<<1, 1, 0, B.st>>>(dst, v);
+    count_launches(1);
+    chk(cudaGetLastError());
+  };
+  // constants of this solve
+  set_scalar(&B.ctl->hv, plan->hvol);
+  set_scalar(&B.ctl->beta, prm->beta);
+  set_scalar(&B.ctl->lam, prm->lambda);
   if (opts->resume && B.valid) {
-    // continue the previous solve of this plan
-    f32 = B.f32 && mixed;
-    if (B.f32 && !mixed) ATKM(SRC_PSI, (const double*)B.phi, nullptr, B.Phi);  // FP64 from here on
-    have_E = !(B.f32 && !mixed);
-    E = B.E; den_prev = B.den_prev; linf = B.linf; force_sd = B.force_sd || (B.f32 && !mixed);
-    have_prev = B.have_prev; caps = B.caps; n = n_start = f32_best_n = B.n;
+    q = B.parity;
+    n = n_start = f32_best_n = B.n;
+    caps = B.caps;
+    linf = B.linf;
+    if (B.f32 && !mixed) {  // continue in FP64 from an FP32-phase state
+      Seq S{plan, B, ph, false, q};
+      S.atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[q]), nullptr, B.Phi[q]);
+      S.ctl1(k_c_reset_state, B.ctl, 0, 1, 0);
+      chk(S.err);
+      f32 = false;
+    } else {
+      f32 = B.f32 && mixed;
+    }
   } else {
-    // Normalise psi0 into phi.
+    // Normalise psi_0 into phi, Phi_0 by ATKM (Step 1 at n = 0).
+    Seq S{plan, B, ph, f32, 0};
     const double2* psi = reinterpret_cast<const double2*>(psi_inout);
-    d.dots({{psi, psi}}, S_N);
-    d.fetch(S_N, S_N + 1);
-    if (d.err != cudaSuccess) return fail_cuda();
-    const double n0 = sqrt(hv * d.h(S_N));
-    if (!(n0 > 0.0) || !isfinite(n0)) {
+    S.dots({{psi, psi}}, S_N);
+    S.ctl1(k_c_init, B.ctl, (const double*)plan->scal);
+    S.lincomb(B.phi[0], psi, Coef{&B.ctl->inv0, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr, Coef{nullptr, 0.0},
+              nullptr, S_T);
+    S.atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[0]), nullptr, B.Phi[0]);
+    S.ctl1(k_c_reset_state, B.ctl, 0, 1, 1);
+    chk(S.err);
+    fetch();
+    if (err != cudaSuccess) return cuda_fail(plan, err, "pcg_ground_state");
+    if (H.nan) {
       out->status = ATKM_ERR_NAN;
       B.valid = false;
       return fail(plan, ATKM_ERR_NAN, "pcg_ground_state: initial state has zero or non-finite norm");
     }
-    d.lincomb(B.phi, psi, 1.0 / n0, nullptr, 0, nullptr, 0, nullptr, S_T);
-    ATKM(SRC_PSI, (const double*)B.phi, nullptr, B.Phi);
   }
+  set_scalar(&B.ctl->tolE_eps, 32.0 * (f32 ? eps32 : eps64));
   B.valid = false;  // set again when this call ends cleanly
-  Parts q{};
-  double mu = 0.0, res = 0.0;
-  int logc = 0;
+
+  int status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0, logc = 0;
   while (true) {
-    // ---- Step 2: H phi, mu, r
-    HOP((const double*)B.phi, (double*)B.Hphi, S_H);
-    d.fetch(S_H, S_H + 10);
-    if (d.err != cudaSuccess) return fail_cuda();
-    q = read_parts(d, hv);
-    mu = q.mu;
-    if (!have_E) {
-      E = q.kin + q.rot + q.pot + 0.5 * beta * q.f4 + 0.5 * lam * q.dip;
-      have_E = true;
-    }
-    d.lincomb(B.r, B.Hphi, 1.0, B.phi, -mu, nullptr, 0, nullptr, S_R);
-    d.fetch(S_R, S_R + 1);
-    if (d.err != cudaSuccess) return fail_cuda();
-    res = sqrt(hv * d.h(S_R));
+    Seq S{plan, B, ph, f32, q};
+    chk(run_phase(S, 0, use_graphs));
+    fetch();
+    if (err != cudaSuccess) break;
     atkm_iter_log* L = (logbuf && logc < opts->log_capacity) ? &logbuf[logc] : nullptr;
     if (L) {
       memset(L, 0, sizeof(*L));
-      L->n = n; L->E = E; L->mu = mu; L->residual = res; L->linf_step = linf; L->f32_phase = f32;
+      L->n = n; L->E = H.E; L->mu = H.mu; L->residual = H.res; L->linf_step = linf; L->f32_phase = f32;
       ++logc;
     }
-    if (!isfinite(E) || !isfinite(res) || !isfinite(mu)) { status = ATKM_ERR_NAN; break; }
-    if (f32) {
-      // FP32 stagnation: no halving of the best residual within 100 iterations
-      if (res < 0.5 * f32_best) { f32_best = res; f32_best_n = n; }
-    }
-    if (f32 && (res <= opts->switch_tol || caps >= 2 || n - f32_best_n > 100)) {
-      // hand over to FP64: recompute Phi and H phi in FP64, restart the direction
+    if (H.nan) { status = ATKM_ERR_NAN; break; }
+    if (f32 && H.res < 0.5 * f32_best) { f32_best = H.res; f32_best_n = n; }
+    if (f32 && (H.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > 100)) {
+      // hand over to FP64: recompute Phi in FP64, re-evaluate this phi, restart the direction
       f32 = false;
       caps = 0;
-      force_sd = true;
-      have_E = false;
-      ATKM(SRC_PSI, (const double*)B.phi, nullptr, B.Phi);
+      Seq S64{plan, B, ph, false, q};
+      S64.atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[q]), nullptr, B.Phi[q]);
+      S64.ctl1(k_c_reset_state, B.ctl, 0, 1, 0);
+      chk(S64.err);
+      set_scalar(&B.ctl->tolE_eps, 32.0 * eps64);
       if (L) --logc;
       continue;
     }
-    if (!f32 && (res <= opts->tol_residual || (opts->tol_linf > 0 && linf <= opts->tol_linf))) {
+    if (!f32 && (H.res <= opts->tol_residual || (opts->tol_linf > 0 && linf <= opts->tol_linf))) {
       status = ATKM_OK;
       break;
     }
     if (n - n_start >= opts->max_iter) { status = ATKM_NOT_CONVERGED; break; }
     if (f32) ++f32_iters;
-    // ---- Step 3: preconditioned PR+ direction
-    const double alpha = q.kin + q.pot + beta * q.f4 + fabs(lam * q.dip);
-    k_set_scalar<<<1, 1, 0, d.st>>>(plan->scal + SC_ALPHA, alpha);
-  count_launches(1);
-    d.chk(cudaGetLastError());
-    PREC();
-    d.dots({{B.Pr, B.phi}, {B.r, B.Pr}, {B.r, B.phi}, {B.rprev, B.Pr}, {B.rprev, B.phi}, {B.pprev, B.phi},
-            {B.phi, B.phi}},
-           S_D);
-    d.fetch(S_D, S_D + 7);
-    if (d.err != cudaSuccess) return fail_cuda();
-    const double b_ = hv * d.h(S_D + 0), rPr = hv * d.h(S_D + 1), rphi = hv * d.h(S_D + 2);
-    const double rpPr = hv * d.h(S_D + 3), a_ = hv * d.h(S_D + 4), c_ = hv * d.h(S_D + 5), nphi = hv * d.h(S_D + 6);
-    const double den = rPr - b_ * rphi;  // <r, J(Pr)>
-    double beta_cg = 0.0;
-    const bool use_cg = have_prev && !force_sd;
-    if (use_cg) {
-      const double jrj = rpPr - 2.0 * a_ * b_ + a_ * b_ * nphi;  // <J(r_prev), J(Pr)>
-      beta_cg = std::max((den - jrj) / den_prev, 0.0);
-      d.lincomb(B.p, B.Pr, -1.0, B.pprev, beta_cg, B.phi, b_ - beta_cg * c_, B.Hphi, S_P);
-    } else {
-      d.lincomb(B.p, B.Pr, -1.0, B.phi, b_, nullptr, 0, B.Hphi, S_P);
+    // Step 4 (iii): halve until the energy decreases (rare)
+    bool nanE = !isfinite(H.En);
+    while (!H.accepted && !nanE && H.nh < opts->max_halvings) {
+      chk(run_phase(S, 1, use_graphs));
+      fetch();
+      if (err != cudaSuccess) break;
+      nanE = !isfinite(H.En);
     }
-    d.fetch(S_P, S_P + 2);
-    if (d.err != cudaSuccess) return fail_cuda();
-    double pn2 = hv * d.h(S_P), d1 = hv * d.h(S_P + 1);
-    bool reset = false;
-    if (d1 >= 0.0) {  // Step 4 (i): PSD fallback
-      reset = true;
-      beta_cg = 0.0;
-      if (use_cg) {
-        d.lincomb(B.p, B.Pr, -1.0, B.phi, b_, nullptr, 0, B.Hphi, S_P);
-        d.fetch(S_P, S_P + 2);
-        if (d.err != cudaSuccess) return fail_cuda();
-        pn2 = hv * d.h(S_P);
-        d1 = hv * d.h(S_P + 1);
-      }
-    }
-    // ---- Step 4 (ii): quadratic model
-    HOP((const double*)B.p, (double*)B.Hp, -1);
-    ATKM(SRC_PAIR, (const double*)B.phi, (const double*)B.p, B.Phi1);
-    d.dots({{B.Hp, B.p}}, S_C);
-    {
-      const int G = red_grid(B.N);
-      k_curv_sums<<<G, kRedThreads, 0, d.st>>>(B.phi, B.p, B.Phi, B.Phi1, beta, lam, B.N, plan->partials);
-      count_launches(1);
-      d.chk(cudaGetLastError());
-      d.chk(launch_finalize(plan, 3, G, S_C + 1, d.st));
-    }
-    d.fetch(S_C, S_C + 4);
-    if (d.err != cudaSuccess) return fail_cuda();
-    const double Hpp = hv * d.h(S_C), S1 = hv * d.h(S_C + 1), S2 = hv * d.h(S_C + 2), S3 = hv * d.h(S_C + 3);
-    const double curv = Hpp + 2.0 * S1 - mu * pn2;
-    double t = curv > 0.0 ? -d1 / curv : 0.3;
-    const double t0 = t;
-    const double pn = sqrt(pn2);
-    const double Aphiphi = q.kin + q.rot + q.pot;
-    const double Aphip = d1 - S2, App = Hpp - S3;
-    // ---- Step 4 (iii) + Step 5: retract, renormalise, test the energy
-    const double tolE = 32.0 * (f32 ? eps32 : eps64) * fabs(E);
-    bool accepted = false;
-    int nh = 0;
-    double bestE = INFINITY, best_t = t, En = 0.0;
-    auto trial = [&](double tt, double& Eout, double& linf_out) {
-      const double c = cos(tt * pn), sn = sin(tt * pn) / pn;
-      d.lincomb(B.phin, B.phi, c, B.p, sn, nullptr, 0, nullptr, S_T);
-      d.fetch(S_T, S_T + 1);
-      const double nrm2 = hv * d.h(S_T);
-      const int G = red_grid(B.N);
-      k_scale_linf<<<G, kRedThreads, 0, d.st>>>(B.phin, B.phi, 1.0 / sqrt(nrm2), B.N, plan->partials);
-      count_launches(1);
-      d.chk(cudaGetLastError());
-      k_finalize_max<<<1, kRedThreads, 0, d.st>>>(plan->partials, G, plan->scal + S_L);
-      count_launches(1);
-      d.chk(cudaGetLastError());
-      ATKM(SRC_PSI, (const double*)B.phin, nullptr, B.Phin);
-      k_quartic_sums<<<G, kRedThreads, 0, d.st>>>(B.phin, B.Phin, B.N, plan->partials);
-      count_launches(1);
-      d.chk(cudaGetLastError());
-      d.chk(launch_finalize(plan, 2, G, S_Q, d.st));
-      d.fetch(S_Q, S_L + 1);
-      const double quad = (c * c * Aphiphi + 2.0 * c * sn * Aphip + sn * sn * App) / nrm2;
-      Eout = quad + 0.5 * beta * hv * d.h(S_Q) + 0.5 * lam * hv * d.h(S_Q + 1);
-      linf_out = d.h(S_L);
-    };
-    double linf_new = 0.0;
-    while (true) {
-      trial(t, En, linf_new);
-      if (d.err != cudaSuccess) return fail_cuda();
-      if (!isfinite(En)) break;
-      if (En <= E + tolE) { accepted = true; break; }
-      if (En < bestE) { bestE = En; best_t = t; }
-      if (nh >= opts->max_halvings) break;
-      t *= 0.5;
-      ++nh;
-    }
-    total_h += nh;
-    if (!isfinite(En)) { status = ATKM_ERR_NAN; break; }
-    if (accepted) {
-      caps = 0;
-      force_sd = false;
-    } else {
-      t = best_t;
-      trial(t, En, linf_new);
-      if (d.err != cudaSuccess) return fail_cuda();
+    if (err != cudaSuccess) break;
+    if (nanE) { status = ATKM_ERR_NAN; break; }
+    total_h += H.nh;
+    const bool accepted = H.accepted;
+    const int nh = H.nh;
+    if (!accepted) {  // take the lowest-energy trial, force steepest descent next
+      chk(run_phase(S, 2, use_graphs));
+      fetch();
+      if (err != cudaSuccess) break;
       ++caps;
-      force_sd = true;
+    } else {
+      caps = 0;
     }
     if (L) {
-      L->alpha = alpha; L->beta_cg = beta_cg; L->reset_to_sd = reset; L->d1 = d1; L->curvature = curv;
-      L->t0 = t0; L->t = t; L->halvings = nh; L->accepted = accepted;
+      L->alpha = H.alpha; L->beta_cg = H.beta_cg; L->reset_to_sd = H.reset; L->d1 = H.d1; L->curvature = H.curv;
+      L->t0 = H.t0; L->t = H.t; L->halvings = nh; L->accepted = accepted;
     }
-    linf = linf_new;
-    std::swap(B.rprev, B.r);
-    std::swap(B.pprev, B.p);
-    std::swap(B.phi, B.phin);
-    std::swap(B.Phi, B.Phin);
-    den_prev = den;
-    have_prev = true;
-    E = En;
+    linf = H.linf;
+    S.ctl1(k_c_end, B.ctl);
+    chk(S.err);
+    q ^= 1;
     ++n;
     if (caps >= 3 && !f32) {
       status = ATKM_STAGNATED;
-      HOP((const double*)B.phi, (double*)B.Hphi, S_H);
-      d.fetch(S_H, S_H + 10);
-      if (d.err != cudaSuccess) return fail_cuda();
-      q = read_parts(d, hv);
-      mu = q.mu;
-      d.lincomb(B.r, B.Hphi, 1.0, B.phi, -mu, nullptr, 0, nullptr, S_R);
-      d.fetch(S_R, S_R + 1);
-      res = sqrt(hv * d.h(S_R));
+      Seq T{plan, B, ph, false, q};
+      T.top();
+      chk(T.err);
+      fetch();
       break;
     }
   }
-  // Keep the scalar state for a later resume, copy the state back and report.
+  if (err != cudaSuccess) {
+    out->status = ATKM_ERR_CUDA;
+    return cuda_fail(plan, err, "pcg_ground_state");
+  }
+  // Keep the state for a later resume, copy phi back and report.
   B.valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED);
-  B.f32 = f32; B.have_prev = have_prev; B.force_sd = force_sd; B.n = n; B.caps = caps;
-  B.E = E; B.den_prev = den_prev; B.linf = linf;
-  d.chk(cudaMemcpyAsync(psi_inout, B.phi, B.N * sizeof(double2), cudaMemcpyDeviceToDevice, d.st));
-  d.chk(cudaStreamSynchronize(d.st));
-  if (d.err != cudaSuccess) return fail_cuda();
-  out->E_kin = q.kin;
-  out->E_rot = q.rot;
-  out->E_pot = q.pot;
-  out->E_int = 0.5 * beta * q.f4;
-  out->E_dip = 0.5 * lam * q.dip;
+  B.f32 = f32; B.parity = q; B.n = n; B.caps = caps; B.linf = linf;
+  chk(cudaMemcpyAsync(psi_inout, B.phi[q], B.N * sizeof(double2), cudaMemcpyDeviceToDevice, B.st));
+  chk(cudaEventRecord(B.ev_out, B.st));
+  chk(cudaStreamWaitEvent(caller, B.ev_out, 0));
+  chk(cudaStreamSynchronize(B.st));
+  if (err != cudaSuccess) {
+    out->status = ATKM_ERR_CUDA;
+    return cuda_fail(plan, err, "pcg_ground_state");
+  }
+  out->E_kin = H.kin;
+  out->E_rot = H.rot;
+  out->E_pot = H.pot;
+  out->E_int = 0.5 * prm->beta * H.f4;
+  out->E_dip = 0.5 * prm->lambda * H.dip;
   out->E = out->E_kin + out->E_rot + out->E_pot + out->E_int + out->E_dip;
-  out->mu = mu;
+  out->mu = H.mu;
   out->virial = 2 * out->E_kin - 2 * out->E_pot + 3 * out->E_int + 3 * out->E_dip;
-  out->residual = res;
+  out->residual = H.res;
   out->linf_step = linf;
   out->iters = n;
   out->halvings = total_h;

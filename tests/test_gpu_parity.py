@@ -242,3 +242,34 @@ def test_cfg3_dipolar_potential_full_size(lib):
     assert rel2(got, ref) <= 1e-11
     got32 = host(plan.dipolar_potential_from_psi(dev(psi), f32=True))
     assert rel2(got32, ref) <= 2e-6
+
+
+def test_graph_replay_is_bitwise_identical_to_direct_launches(lib):
+    w = W.CONFIGS["cfg2_128x128x32"]
+    plan = lib.Plan(w.N, w.L, w.n, f32=True)
+    prm = lib.make_params(w.gamma, w.beta, w.lam, w.Omega)
+    outs = []
+    for graphs in (True, False):
+        for prec in (0, 1):
+            psi = dev(W.initial_guess(w))
+            r = plan.pcg_ground_state(prm, psi, max_iter=12, precision=prec, graphs=graphs, log_capacity=20)
+            outs.append((graphs, prec, host(psi), [l["E"] for l in r["log"]]))
+    for prec in (0, 1):
+        a = [o for o in outs if o[0] and o[1] == prec][0]
+        b = [o for o in outs if not o[0] and o[1] == prec][0]
+        assert np.array_equal(a[2], b[2])
+        assert a[3] == b[3]
+
+
+def test_resume_continues_the_same_solve(lib):
+    w = W.CONFIGS["cfg1_32x32x16"]
+    plan = lib.Plan(w.N, w.L, w.n)
+    prm = lib.make_params(w.gamma, w.beta, w.lam, w.Omega)
+    psi1 = dev(W.initial_guess(w))
+    r1 = plan.pcg_ground_state(prm, psi1, max_iter=20, tol_residual=0.0)
+    psi2 = dev(W.initial_guess(w))
+    plan.pcg_ground_state(prm, psi2, max_iter=8, tol_residual=0.0)
+    r2 = plan.pcg_ground_state(prm, psi2, max_iter=12, tol_residual=0.0, resume=True)
+    assert r2["iters"] == 20 == r1["iters"]
+    assert np.array_equal(host(psi1), host(psi2))
+    assert r1["E"] == r2["E"]
