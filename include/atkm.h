@@ -239,6 +239,22 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
                      double* psi_inout, atkm_result* out, void* stream);
 
 /*
+ * pcg_ground_state_batched -- `count` independent solves of Algorithm 1 (an
+ * Omega or anisotropy sweep) on one GPU.  Grids may differ: instance i uses
+ * plans[i] (each instance needs its own plan), prm[i], psi[i] (device, in/out)
+ * and out[i] (its log pointer is honoured); all share `opts`.  Each batched
+ * round replays every active instance's captured iteration graph on that
+ * instance's plan stream, so instances run concurrently on the GPU, then
+ * reads all control blocks with one synchronisation per stream.  Results are
+ * bitwise identical to pcg_ground_state on each instance alone.  Returns
+ * ATKM_OK if every instance converged, else the first non-OK status
+ * (ATKM_ERR_CUDA takes precedence); per-instance statuses are in out[i].status.
+ */
+int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_params* prm,
+                             const atkm_pcg_opts* opts, double* const* psi, atkm_result* out,
+                             void* stream);
+
+/*
  * atkm_inner_products_noalloc -- out[i] = hvol * Re(sum_j u_i[j] conj(v_i[j]))
  * for i < npairs, without allocating anything.  The paper has no counterpart:
  * this is for callers that cannot call cudaMalloc (code inside a host

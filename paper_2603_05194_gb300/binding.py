@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         "atkm_energy_parts": (ip, [vp, C.POINTER(Params), vp, vp, C.POINTER(Energy), vp]),
         "apply_preconditioner": (ip, [vp, C.POINTER(Params), C.c_double, vp, vp, vp, vp, vp]),
         "pcg_ground_state": (ip, [vp, C.POINTER(Params), C.POINTER(PcgOpts), vp, C.POINTER(Result), vp]),
+        "pcg_ground_state_batched": (ip, [C.c_int, C.POINTER(vp), C.POINTER(Params), C.POINTER(PcgOpts),
+                                          C.POINTER(vp), C.POINTER(Result), vp]),
         "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
         "atkm_launch_count": (C.c_ulonglong, []),
         "atkm_inner_products_noalloc": (ip, [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_ulonglong, C.c_double, vp,
@@ -108,6 +110,32 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, max_iter=10000, max_halvings=20,
+                             precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True) -> list:
+    """Runs independent solves (one plan each, grids may differ) concurrently
+    through pcg_ground_state_batched; returns one result dict per instance."""
+    lib = load_library()
+    n = len(plans)
+    if not (n == len(params) == len(psis)) or n == 0:
+        raise ValueError("plans, params and psis must have the same, non-zero length")
+    for pl, ps in zip(plans, psis):
+        _ptr(ps, torch.complex128, pl.shape, "psi")
+    opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1)
+    ph = (C.c_void_p * n)(*[pl._h for pl in plans])
+    pa = (Params * n)(*params)
+    pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
+    res = (Result * n)()
+    code = lib.pcg_ground_state_batched(n, ph, pa, C.byref(opts), pp, res, _stream(stream))
+    if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN):
+        raise AtkmError(code, lib.atkm_last_error_string(None).decode())
+    outs = []
+    for i in range(n):
+        d = {k: getattr(res[i], k) for k, _ in Result._fields_ if k != "log"}
+        d["status_name"] = STATUS_NAMES.get(res[i].status, str(res[i].status))
+        outs.append(d)
+    return outs
 
 
 def inner_products_noalloc(us, vs, hvol: float, out: torch.Tensor, stream=None) -> torch.Tensor:

@@ -603,6 +603,263 @@ static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   return cudaGraphLaunch(gx, B.st);
 }
 
+// One PCG solve as a host-side state machine: launch() enqueues the next
+// phase (graph or direct launches) and an asynchronous read of the control
+// block on the plan stream; wait() synchronises that stream; process() takes
+// the decisions of the stop rule, the halving loop and the log.  Several
+// solvers on different plans run concurrently (pcg_ground_state_batched).
+struct Solver {
+  enum State { INIT_CHECK, MAIN, HALVE, FORCED, FINAL, DONE };
+  atkm_plan* plan = nullptr;
+  const atkm_params* prm = nullptr;
+  const atkm_pcg_opts* opts = nullptr;
+  double* psi = nullptr;
+  atkm_result* out = nullptr;
+  atkm_iter_log* logbuf = nullptr;
+  PcgBuffers* B = nullptr;
+  cudaStream_t caller = nullptr;
+  Phys ph{};
+  bool mixed = false, use_graphs = true, f32 = false, began = false;
+  int q = 0, n = 0, n_start = 0, caps = 0, status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0, logc = 0;
+  int f32_best_n = 0, early_code = ATKM_OK;
+  double linf = INFINITY, f32_best = INFINITY;
+  State st = DONE;
+  atkm_iter_log* L = nullptr;
+  cudaError_t err = cudaSuccess;
+  const double eps64 = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
+
+  void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
+  bool done() const { return st == DONE || err != cudaSuccess; }
+  Ctl& H() { return *B->ctl_h; }
+  Seq seq(bool is32) { return Seq{plan, *B, ph, is32, q}; }
+  void fetch_async() { chk(cudaMemcpyAsync(B->ctl_h, B->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, B->st)); }
+  void set_scalar(double* dst, double v) {
+    k_set_scalar<<<1, 1, 0, B->st>>>(dst, v);
+    count_launches(1);
+    chk(cudaGetLastError());
+  }
+
+  int begin(atkm_plan* pl, const atkm_params* pr, const atkm_pcg_opts* op, double* ps, atkm_result* o,
+            cudaStream_t cs) {
+    plan = pl; prm = pr; opts = op; psi = ps; out = o; caller = cs;
+    if (!plan || !prm || !opts || !psi || !out) return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: NULL argument");
+    if (!(opts->tol_residual >= 0.0) || opts->max_iter < 0 || opts->max_halvings < 0)
+      return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: bad options");
+    mixed = opts->precision_mode == ATKM_PRECISION_F32_F64;
+    if (opts->precision_mode != ATKM_PRECISION_F64 && !mixed)
+      return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: unknown precision_mode");
+    if (mixed && !(plan->flags & ATKM_PLAN_F32))
+      return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: mixed precision needs a plan created with ATKM_PLAN_F32");
+    logbuf = out->log;
+    memset(out, 0, sizeof(*out));
+    out->log = logbuf;
+    cudaError_t ae = pcg_alloc(plan);
+    if (ae != cudaSuccess) return cuda_fail(plan, ae, "pcg_ground_state: allocation");
+    B = plan->pcg;
+    ph = make_phys(prm);
+    if (B->gphys_set && memcmp(&B->gphys, &ph, sizeof(Phys)) != 0) destroy_graphs(B);
+    B->gphys = ph;
+    B->gphys_set = true;
+    use_graphs = (plan->prof == nullptr) && !opts->no_graphs;
+    began = true;
+    chk(cudaEventRecord(B->ev_in, caller));  // order after the caller's prior work
+    chk(cudaStreamWaitEvent(B->st, B->ev_in, 0));
+    set_scalar(&B->ctl->hv, plan->hvol);
+    set_scalar(&B->ctl->beta, prm->beta);
+    set_scalar(&B->ctl->lam, prm->lambda);
+    f32 = mixed;
+    if (opts->resume && B->valid) {
+      q = B->parity;
+      n = n_start = f32_best_n = B->n;
+      caps = B->caps;
+      linf = B->linf;
+      if (B->f32 && !mixed) {  // continue in FP64 from an FP32-phase state
+        Seq S = seq(false);
+        S.atkm(SRC_PSI, reinterpret_cast<const double*>(B->phi[q]), nullptr, B->Phi[q]);
+        S.ctl1(k_c_reset_state, B->ctl, 0, 1, 0);
+        chk(S.err);
+        f32 = false;
+      } else {
+        f32 = B->f32 && mixed;
+      }
+      st = MAIN;
+    } else {
+      // Normalise psi_0 into phi, Phi_0 by ATKM (Step 1 at n = 0).
+      q = 0;
+      Seq S = seq(f32);
+      const double2* p0 = reinterpret_cast<const double2*>(psi);
+      S.dots({{p0, p0}}, S_N);
+      S.ctl1(k_c_init, B->ctl, (const double*)plan->scal);
+      S.lincomb(B->phi[0], p0, Coef{&B->ctl->inv0, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr, Coef{nullptr, 0.0},
+                nullptr, S_T);
+      S.atkm(SRC_PSI, reinterpret_cast<const double*>(B->phi[0]), nullptr, B->Phi[0]);
+      S.ctl1(k_c_reset_state, B->ctl, 0, 1, 1);
+      chk(S.err);
+      fetch_async();
+      st = INIT_CHECK;
+    }
+    set_scalar(&B->ctl->tolE_eps, 32.0 * (f32 ? eps32 : eps64));
+    B->valid = false;  // set again when this solve ends cleanly
+    return ATKM_OK;
+  }
+
+  void launch() {
+    if (st == INIT_CHECK) return;  // its work is already enqueued
+    Seq S = seq(f32);
+    if (st == MAIN) chk(run_phase(S, 0, use_graphs));
+    else if (st == HALVE) chk(run_phase(S, 1, use_graphs));
+    else if (st == FORCED) chk(run_phase(S, 2, use_graphs));
+    else if (st == FINAL) { S.top(); chk(S.err); }
+    fetch_async();
+  }
+
+  void wait() { chk(cudaStreamSynchronize(B->st)); }
+
+  void finish_iteration(bool accepted) {
+    Ctl& h = H();
+    total_h += h.nh;
+    if (accepted) caps = 0;
+    else ++caps;
+    if (L) {
+      L->alpha = h.alpha; L->beta_cg = h.beta_cg; L->reset_to_sd = h.reset; L->d1 = h.d1; L->curvature = h.curv;
+      L->t0 = h.t0; L->t = h.t; L->halvings = h.nh; L->accepted = accepted;
+    }
+    linf = h.linf;
+    Seq S = seq(f32);
+    S.ctl1(k_c_end, B->ctl);
+    chk(S.err);
+    q ^= 1;
+    ++n;
+    if (caps >= 3 && !f32) {
+      status = ATKM_STAGNATED;
+      st = FINAL;
+    } else {
+      st = MAIN;
+    }
+  }
+
+  void process() {
+    if (err != cudaSuccess) return;
+    Ctl& h = H();
+    switch (st) {
+      case INIT_CHECK:
+        if (h.nan) {
+          status = ATKM_ERR_NAN;
+          early_code = ATKM_ERR_NAN;
+          st = DONE;
+        } else {
+          st = MAIN;
+        }
+        return;
+      case MAIN: {
+        L = (logbuf && logc < opts->log_capacity) ? &logbuf[logc] : nullptr;
+        if (L) {
+          memset(L, 0, sizeof(*L));
+          L->n = n; L->E = h.E; L->mu = h.mu; L->residual = h.res; L->linf_step = linf; L->f32_phase = f32;
+          ++logc;
+        }
+        if (h.nan) { status = ATKM_ERR_NAN; st = DONE; return; }
+        if (f32 && h.res < 0.5 * f32_best) { f32_best = h.res; f32_best_n = n; }
+        if (f32 && (h.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > 100)) {
+          // hand over to FP64: recompute Phi in FP64, re-evaluate this phi, restart the direction
+          f32 = false;
+          caps = 0;
+          Seq S = seq(false);
+          S.atkm(SRC_PSI, reinterpret_cast<const double*>(B->phi[q]), nullptr, B->Phi[q]);
+          S.ctl1(k_c_reset_state, B->ctl, 0, 1, 0);
+          chk(S.err);
+          set_scalar(&B->ctl->tolE_eps, 32.0 * eps64);
+          if (L) { --logc; L = nullptr; }
+          st = MAIN;
+          return;
+        }
+        if (!f32 && (h.res <= opts->tol_residual || (opts->tol_linf > 0 && linf <= opts->tol_linf))) {
+          status = ATKM_OK;
+          st = DONE;
+          return;
+        }
+        if (n - n_start >= opts->max_iter) { status = ATKM_NOT_CONVERGED; st = DONE; return; }
+        if (f32) ++f32_iters;
+        decide_trial();
+        return;
+      }
+      case HALVE:
+        decide_trial();
+        return;
+      case FORCED:
+        finish_iteration(false);
+        return;
+      case FINAL:
+        st = DONE;
+        return;
+      default:
+        return;
+    }
+  }
+
+  // Step 4 (iii) after a trial: accept, halve again, or take the best trial.
+  void decide_trial() {
+    Ctl& h = H();
+    if (!isfinite(h.En)) { status = ATKM_ERR_NAN; st = DONE; return; }
+    if (h.accepted) { finish_iteration(true); return; }
+    st = (h.nh < opts->max_halvings) ? HALVE : FORCED;
+  }
+
+  // Called when another instance failed before this one started iterating.
+  void abandon() {
+    if (began && B) cudaStreamSynchronize(B->st);
+  }
+
+  int end() {
+    if (!began) return early_code;
+    if (err != cudaSuccess) {
+      out->status = ATKM_ERR_CUDA;
+      cudaStreamSynchronize(B->st);
+      return cuda_fail(plan, err, "pcg_ground_state");
+    }
+    if (early_code == ATKM_ERR_NAN) {
+      out->status = ATKM_ERR_NAN;
+      B->valid = false;
+      chk(cudaEventRecord(B->ev_out, B->st));
+      chk(cudaStreamWaitEvent(caller, B->ev_out, 0));
+      return fail(plan, ATKM_ERR_NAN, "pcg_ground_state: initial state has zero or non-finite norm");
+    }
+    Ctl& h = H();
+    B->valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED);
+    B->f32 = f32; B->parity = q; B->n = n; B->caps = caps; B->linf = linf;
+    chk(cudaMemcpyAsync(psi, B->phi[q], B->N * sizeof(double2), cudaMemcpyDeviceToDevice, B->st));
+    chk(cudaEventRecord(B->ev_out, B->st));
+    chk(cudaStreamWaitEvent(caller, B->ev_out, 0));
+    chk(cudaStreamSynchronize(B->st));
+    if (err != cudaSuccess) {
+      out->status = ATKM_ERR_CUDA;
+      return cuda_fail(plan, err, "pcg_ground_state");
+    }
+    out->E_kin = h.kin;
+    out->E_rot = h.rot;
+    out->E_pot = h.pot;
+    out->E_int = 0.5 * prm->beta * h.f4;
+    out->E_dip = 0.5 * prm->lambda * h.dip;
+    out->E = out->E_kin + out->E_rot + out->E_pot + out->E_int + out->E_dip;
+    out->mu = h.mu;
+    out->virial = 2 * out->E_kin - 2 * out->E_pot + 3 * out->E_int + 3 * out->E_dip;
+    out->residual = h.res;
+    out->linf_step = linf;
+    out->iters = n;
+    out->halvings = total_h;
+    out->f32_iters = f32_iters;
+    out->status = status;
+    out->log_count = logc;
+    if (status != ATKM_OK) {
+      const char* why = status == ATKM_NOT_CONVERGED ? "max_iter reached"
+                        : status == ATKM_STAGNATED   ? "three consecutive exhausted halving loops"
+                                                     : "non-finite energy or residual";
+      fail(plan, status, std::string("pcg_ground_state: ") + why);
+    }
+    return status;
+  }
+};
+
 }  // namespace atkm
 
 using namespace atkm;
@@ -648,196 +905,54 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
 
 int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opts* opts, double* psi_inout,
                      atkm_result* out, void* stream) {
-  if (!plan || !prm || !opts || !psi_inout || !out) return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: NULL argument");
-  if (!(opts->tol_residual >= 0.0) || opts->max_iter < 0 || opts->max_halvings < 0)
-    return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: bad options");
-  const bool mixed = opts->precision_mode == ATKM_PRECISION_F32_F64;
-  if (opts->precision_mode != ATKM_PRECISION_F64 && !mixed)
-    return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: unknown precision_mode");
-  if (mixed && !(plan->flags & ATKM_PLAN_F32))
-    return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: mixed precision needs a plan created with ATKM_PLAN_F32");
-  atkm_iter_log* logbuf = out->log;
-  memset(out, 0, sizeof(*out));
-  out->log = logbuf;
-  cudaError_t ae = pcg_alloc(plan);
-  if (ae != cudaSuccess) return cuda_fail(plan, ae, "pcg_ground_state: allocation");
-  PcgBuffers& B = *plan->pcg;
-  cudaStream_t caller = (cudaStream_t)stream;
-  const Phys ph = make_phys(prm);
-  if (B.gphys_set && memcmp(&B.gphys, &ph, sizeof(Phys)) != 0) destroy_graphs(&B);
-  B.gphys = ph;
-  B.gphys_set = true;
-  const bool use_graphs = (plan->prof == nullptr) && !opts->no_graphs;
-  const double eps64 = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
-  cudaError_t err = cudaSuccess;
-  auto chk = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; };
-  // order after the caller's prior work
-  chk(cudaEventRecord(B.ev_in, caller));
-  chk(cudaStreamWaitEvent(B.st, B.ev_in, 0));
-
-  bool f32 = mixed;
-  int q = 0, n = 0, n_start = 0, caps = 0;
-  double linf = INFINITY;
-  double f32_best = INFINITY;
-  int f32_best_n = 0;
-  Ctl& H = *B.ctl_h;
-  auto fetch = [&]() {
-    chk(cudaMemcpyAsync(B.ctl_h, B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, B.st));
-    chk(cudaStreamSynchronize(B.st));
-  };
-  auto set_scalar = [&](double* dst, double v) {
-    k_set_scalar<<<1, 1, 0, B.st>>>(dst, v);
-    count_launches(1);
-    chk(cudaGetLastError());
-  };
-  // constants of this solve
-  set_scalar(&B.ctl->hv, plan->hvol);
-  set_scalar(&B.ctl->beta, prm->beta);
-  set_scalar(&B.ctl->lam, prm->lambda);
-  if (opts->resume && B.valid) {
-    q = B.parity;
-    n = n_start = f32_best_n = B.n;
-    caps = B.caps;
-    linf = B.linf;
-    if (B.f32 && !mixed) {  // continue in FP64 from an FP32-phase state
-      Seq S{plan, B, ph, false, q};
-      S.atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[q]), nullptr, B.Phi[q]);
-      S.ctl1(k_c_reset_state, B.ctl, 0, 1, 0);
-      chk(S.err);
-      f32 = false;
-    } else {
-      f32 = B.f32 && mixed;
-    }
-  } else {
-    // Normalise psi_0 into phi, Phi_0 by ATKM (Step 1 at n = 0).
-    Seq S{plan, B, ph, f32, 0};
-    const double2* psi = reinterpret_cast<const double2*>(psi_inout);
-    S.dots({{psi, psi}}, S_N);
-    S.ctl1(k_c_init, B.ctl, (const double*)plan->scal);
-    S.lincomb(B.phi[0], psi, Coef{&B.ctl->inv0, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr, Coef{nullptr, 0.0},
-              nullptr, S_T);
-    S.atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[0]), nullptr, B.Phi[0]);
-    S.ctl1(k_c_reset_state, B.ctl, 0, 1, 1);
-    chk(S.err);
-    fetch();
-    if (err != cudaSuccess) return cuda_fail(plan, err, "pcg_ground_state");
-    if (H.nan) {
-      out->status = ATKM_ERR_NAN;
-      B.valid = false;
-      return fail(plan, ATKM_ERR_NAN, "pcg_ground_state: initial state has zero or non-finite norm");
-    }
+  Solver S;
+  int code = S.begin(plan, prm, opts, psi_inout, out, (cudaStream_t)stream);
+  if (code != ATKM_OK) return code;
+  while (!S.done()) {
+    S.launch();
+    S.wait();
+    S.process();
   }
-  set_scalar(&B.ctl->tolE_eps, 32.0 * (f32 ? eps32 : eps64));
-  B.valid = false;  // set again when this call ends cleanly
+  return S.end();
+}
 
-  int status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0, logc = 0;
+int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_params* prm, const atkm_pcg_opts* opts,
+                             double* const* psi, atkm_result* out, void* stream) {
+  if (count < 1 || !plans || !prm || !opts || !psi || !out)
+    return fail(nullptr, ATKM_ERR_ARG, "pcg_ground_state_batched: bad count or NULL argument");
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < i; ++j)
+      if (plans[i] == plans[j])
+        return fail(nullptr, ATKM_ERR_ARG, "pcg_ground_state_batched: each instance needs its own plan");
+  std::vector<Solver> S(count);
+  int first_err = ATKM_OK;
+  for (int i = 0; i < count; ++i) {
+    const int code = S[i].begin(plans[i], &prm[i], opts, psi[i], &out[i], (cudaStream_t)stream);
+    if (code != ATKM_OK && first_err == ATKM_OK) first_err = code;
+  }
+  if (first_err != ATKM_OK) {
+    for (int i = 0; i < count; ++i) S[i].abandon();
+    return first_err;
+  }
+  // One batched round: every active instance enqueues its next phase on its
+  // own stream (they overlap on the GPU), then all are awaited and processed.
   while (true) {
-    Seq S{plan, B, ph, f32, q};
-    chk(run_phase(S, 0, use_graphs));
-    fetch();
-    if (err != cudaSuccess) break;
-    atkm_iter_log* L = (logbuf && logc < opts->log_capacity) ? &logbuf[logc] : nullptr;
-    if (L) {
-      memset(L, 0, sizeof(*L));
-      L->n = n; L->E = H.E; L->mu = H.mu; L->residual = H.res; L->linf_step = linf; L->f32_phase = f32;
-      ++logc;
-    }
-    if (H.nan) { status = ATKM_ERR_NAN; break; }
-    if (f32 && H.res < 0.5 * f32_best) { f32_best = H.res; f32_best_n = n; }
-    if (f32 && (H.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > 100)) {
-      // hand over to FP64: recompute Phi in FP64, re-evaluate this phi, restart the direction
-      f32 = false;
-      caps = 0;
-      Seq S64{plan, B, ph, false, q};
-      S64.atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[q]), nullptr, B.Phi[q]);
-      S64.ctl1(k_c_reset_state, B.ctl, 0, 1, 0);
-      chk(S64.err);
-      set_scalar(&B.ctl->tolE_eps, 32.0 * eps64);
-      if (L) --logc;
-      continue;
-    }
-    if (!f32 && (H.res <= opts->tol_residual || (opts->tol_linf > 0 && linf <= opts->tol_linf))) {
-      status = ATKM_OK;
-      break;
-    }
-    if (n - n_start >= opts->max_iter) { status = ATKM_NOT_CONVERGED; break; }
-    if (f32) ++f32_iters;
-    // Step 4 (iii): halve until the energy decreases (rare)
-    bool nanE = !isfinite(H.En);
-    while (!H.accepted && !nanE && H.nh < opts->max_halvings) {
-      chk(run_phase(S, 1, use_graphs));
-      fetch();
-      if (err != cudaSuccess) break;
-      nanE = !isfinite(H.En);
-    }
-    if (err != cudaSuccess) break;
-    if (nanE) { status = ATKM_ERR_NAN; break; }
-    total_h += H.nh;
-    const bool accepted = H.accepted;
-    const int nh = H.nh;
-    if (!accepted) {  // take the lowest-energy trial, force steepest descent next
-      chk(run_phase(S, 2, use_graphs));
-      fetch();
-      if (err != cudaSuccess) break;
-      ++caps;
-    } else {
-      caps = 0;
-    }
-    if (L) {
-      L->alpha = H.alpha; L->beta_cg = H.beta_cg; L->reset_to_sd = H.reset; L->d1 = H.d1; L->curvature = H.curv;
-      L->t0 = H.t0; L->t = H.t; L->halvings = nh; L->accepted = accepted;
-    }
-    linf = H.linf;
-    S.ctl1(k_c_end, B.ctl);
-    chk(S.err);
-    q ^= 1;
-    ++n;
-    if (caps >= 3 && !f32) {
-      status = ATKM_STAGNATED;
-      Seq T{plan, B, ph, false, q};
-      T.top();
-      chk(T.err);
-      fetch();
-      break;
-    }
+    bool any = false;
+    for (auto& s : S)
+      if (!s.done()) { s.launch(); any = true; }
+    if (!any) break;
+    for (auto& s : S)
+      if (!s.done()) s.wait();
+    for (auto& s : S)
+      if (!s.done()) s.process();
   }
-  if (err != cudaSuccess) {
-    out->status = ATKM_ERR_CUDA;
-    return cuda_fail(plan, err, "pcg_ground_state");
+  int worst = ATKM_OK;
+  for (auto& s : S) {
+    const int code = s.end();
+    if (code != ATKM_OK && worst == ATKM_OK) worst = code;
+    if (code == ATKM_ERR_CUDA) worst = code;
   }
-  // Keep the state for a later resume, copy phi back and report.
-  B.valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED);
-  B.f32 = f32; B.parity = q; B.n = n; B.caps = caps; B.linf = linf;
-  chk(cudaMemcpyAsync(psi_inout, B.phi[q], B.N * sizeof(double2), cudaMemcpyDeviceToDevice, B.st));
-  chk(cudaEventRecord(B.ev_out, B.st));
-  chk(cudaStreamWaitEvent(caller, B.ev_out, 0));
-  chk(cudaStreamSynchronize(B.st));
-  if (err != cudaSuccess) {
-    out->status = ATKM_ERR_CUDA;
-    return cuda_fail(plan, err, "pcg_ground_state");
-  }
-  out->E_kin = H.kin;
-  out->E_rot = H.rot;
-  out->E_pot = H.pot;
-  out->E_int = 0.5 * prm->beta * H.f4;
-  out->E_dip = 0.5 * prm->lambda * H.dip;
-  out->E = out->E_kin + out->E_rot + out->E_pot + out->E_int + out->E_dip;
-  out->mu = H.mu;
-  out->virial = 2 * out->E_kin - 2 * out->E_pot + 3 * out->E_int + 3 * out->E_dip;
-  out->residual = H.res;
-  out->linf_step = linf;
-  out->iters = n;
-  out->halvings = total_h;
-  out->f32_iters = f32_iters;
-  out->status = status;
-  out->log_count = logc;
-  if (status != ATKM_OK) {
-    const char* why = status == ATKM_NOT_CONVERGED ? "max_iter reached"
-                      : status == ATKM_STAGNATED   ? "three consecutive exhausted halving loops"
-                                                   : "non-finite energy or residual";
-    fail(plan, status, std::string("pcg_ground_state: ") + why);
-  }
-  return status;
+  return worst;
 }
 
 }  // extern "C"

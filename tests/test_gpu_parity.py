@@ -273,3 +273,35 @@ def test_resume_continues_the_same_solve(lib):
     assert r2["iters"] == 20 == r1["iters"]
     assert np.array_equal(host(psi1), host(psi2))
     assert r1["E"] == r2["E"]
+
+
+def test_batched_sweep_matches_single_instance_solves(lib):
+    """Uneven grids (radix 2 and 3, fast and generic engines) and different
+    rotation speeds in one batched call: each instance equals its own solve."""
+    cases = [((32, 32, 16), (8.0, 8.0, 2.0), 0.40), ((24, 24, 12), (6.0, 6.0, 1.5), 0.55),
+             ((48, 40, 16), (8.0, 7.0, 2.0), 0.70), ((20, 30, 10), (5.0, 6.0, 1.5), 0.30)]
+    gamma, beta, lam, n = (1.0, 1.0, 4.0), 40.0, 12.0, (0.0, 0.0, 1.0)
+    plans, prms, psis, refs = [], [], [], []
+    for N, L, Om in cases:
+        plans.append(lib.Plan(N, L, n))
+        prms.append(lib.make_params(gamma, beta, lam, Om))
+        psis.append(dev(W.guess_phi_d(N, L, gamma, Om)))
+    for pl, pr, (N, L, Om) in zip(plans, prms, cases):
+        solo = lib.Plan(N, L, n)
+        ps = dev(W.guess_phi_d(N, L, gamma, Om))
+        r = solo.pcg_ground_state(pr, ps, max_iter=80)
+        refs.append((host(ps), r))
+    outs = lib.pcg_ground_state_batched(plans, prms, psis, max_iter=80)
+    for (ref_psi, ref_r), ps, o in zip(refs, psis, outs):
+        assert o["status"] == ref_r["status"] and o["iters"] == ref_r["iters"]
+        assert o["E"] == ref_r["E"]
+        assert np.array_equal(host(ps), ref_psi)
+
+
+def test_batched_rejects_shared_plan(lib):
+    plan = lib.Plan((8, 8, 4), (2.0, 2.0, 1.0), (0, 0, 1))
+    prm = lib.make_params((1, 1, 1), 1.0, 0.0, 0.0)
+    a = dev(W.guess_phi_d((8, 8, 4), (2.0, 2.0, 1.0), (1, 1, 1), 0.0))
+    b = a.clone()
+    with pytest.raises(lib.AtkmError):
+        lib.pcg_ground_state_batched([plan, plan], [prm, prm], [a, b], max_iter=2)
