@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/atkm.h"
 
@@ -296,6 +297,20 @@ void count_launches(int n);
 // Profiling hooks: no-ops unless profiling is on.  `name` must be a literal.
 void prof_begin(atkm_plan* p, const char* name, double bytes, double flops, cudaStream_t st);
 void prof_end(atkm_plan* p, cudaStream_t st);
+
+// Event pair of one pass launch recorded into a captured CUDA graph; every
+// replay re-records the same events.  The owner destroys the events.
+struct ProfRec {
+  const char* name;
+  double bytes, flops;
+  cudaEvent_t a, b;
+};
+// While a sink is set, prof_begin/prof_end record into it with fresh events
+// (for graph capture) instead of the plan's eager record.
+void prof_set_sink(atkm_plan* p, std::vector<ProfRec>* sink);
+// Adds the elapsed times of a replayed graph's records to the plan's totals
+// (call after the replay has completed).
+void prof_accumulate(atkm_plan* p, const std::vector<ProfRec>& recs);
 
 // Launchers (passes.cu).  All enqueue on `st`.
 enum AtkmSrc { SRC_RHO = 0, SRC_PSI = 1, SRC_PAIR = 2 };

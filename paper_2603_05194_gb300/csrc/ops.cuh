@@ -206,13 +206,20 @@ __global__ void __launch_bounds__(kThreads) k_fast(Op op, const cx<R>* __restric
   cx<R> v[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) v[r] = ok ? op.load(o, x, j + C::TPL * r) : czero<R>();
-  for (int i = threadIdx.x; i < L; i += kThreads) tw[i] = twg[i];
+  // FP64 twiddles are staged in shared memory; FP32 twiddles are read through
+  // L1 from global memory, which avoids the bank conflicts of the strided
+  // table accesses (the FP32 passes are issue-bound, the FP64 ones ALU-bound).
+  const cx<R>* twsrc = twg;
+  if (sizeof(R) == 8) {
+    for (int i = threadIdx.x; i < L; i += kThreads) tw[i] = twg[i];
+    twsrc = tw;
+  }
   __syncthreads();
   constexpr int NR = Op::kRed > 0 ? Op::kRed : 1;
   R acc[NR];
 #pragma unroll
   for (int s = 0; s < NR; ++s) acc[s] = (R)0;
-  fast_fft<R, L, Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
+  fast_fft<R, L, Op::kSign1, Op::kLM>(v, b0, b1, twsrc, t, j);
   if constexpr (Op::kMirror) {
     // exchange so every thread sees the frequency L - k of each of its k
     __syncthreads();
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_fast(Op op, const cx<R>* __restric
     }
     if (Op::kSecond) {
       __syncthreads();
-      fast_fft<R, L, -Op::kSign1, Op::kLM>(v, b0, b1, tw, t, j);
+      fast_fft<R, L, -Op::kSign1, Op::kLM>(v, b0, b1, twsrc, t, j);
     }
     if (ok) {
 #pragma unroll

@@ -109,6 +109,28 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(DotPairs dp, size_t N, dou
   block_reduce_store<kMaxDots>(acc, part, gridDim.x, blockIdx.x);
 }
 
+// The seven sums of the direction step from one read of its five vectors:
+// <Pr,phi>, <r,Pr>, <r,phi>, <r_prev,Pr>, <r_prev,phi>, <p_prev,phi>, <phi,phi>
+// (same per-element order as k_dots on the seven pairs).
+__global__ void __launch_bounds__(kRedThreads)
+k_dir_dots(const double2* __restrict__ Pr, const double2* __restrict__ phi, const double2* __restrict__ r,
+           const double2* __restrict__ rp, const double2* __restrict__ pp, size_t N, double* __restrict__ part) {
+  double acc[kMaxDots];
+#pragma unroll
+  for (int i = 0; i < kMaxDots; ++i) acc[i] = 0.0;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
+    const double2 P = Pr[j], f = phi[j], a = r[j], b = rp[j], c = pp[j];
+    acc[0] += P.x * f.x + P.y * f.y;
+    acc[1] += a.x * P.x + a.y * P.y;
+    acc[2] += a.x * f.x + a.y * f.y;
+    acc[3] += b.x * P.x + b.y * P.y;
+    acc[4] += b.x * f.x + b.y * f.y;
+    acc[5] += c.x * f.x + c.y * f.y;
+    acc[6] += f.x * f.x + f.y * f.y;
+  }
+  block_reduce_store<kMaxDots>(acc, part, gridDim.x, blockIdx.x);
+}
+
 // A coefficient m * (*p) (p may be null: then m).
 struct Coef {
   const double* p;
@@ -376,6 +398,9 @@ struct PcgBuffers {
   cudaGraphExec_t gx[2][2][3] = {};
   int gnodes[2][2][3] = {};
   bool seen[2][2][3] = {};
+  bool gprof[2][2][3] = {};                 // captured with profiling events
+  std::vector<ProfRec> grecs[2][2][3];      // those events
+  const std::vector<ProfRec>* last = nullptr;  // records of the last replay
   bool graphs_ok = true;
   Phys gphys{};
   bool gphys_set = false;
@@ -385,13 +410,23 @@ struct PcgBuffers {
   double linf = INFINITY;
 };
 
+static void drop_graph(PcgBuffers* b, int f, int q, int k) {
+  if (b->gx[f][q][k]) { cudaGraphExecDestroy(b->gx[f][q][k]); b->gx[f][q][k] = nullptr; }
+  for (auto& r : b->grecs[f][q][k]) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  b->grecs[f][q][k].clear();
+  b->seen[f][q][k] = false;
+  b->gnodes[f][q][k] = 0;
+  b->gprof[f][q][k] = false;
+}
+
 static void destroy_graphs(PcgBuffers* b) {
-  for (auto& a : b->gx)
-    for (auto& c : a)
-      for (auto& g : c)
-        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
-  memset(b->seen, 0, sizeof(b->seen));
-  memset(b->gnodes, 0, sizeof(b->gnodes));
+  for (int f = 0; f < 2; ++f)
+    for (int q = 0; q < 2; ++q)
+      for (int k = 0; k < 3; ++k) drop_graph(b, f, q, k);
+  b->last = nullptr;
 }
 
 void pcg_free(atkm_plan* p) {
@@ -456,14 +491,19 @@ struct Seq {
     DotPairs dp;
     memset(&dp, 0, sizeof(dp));
     for (auto& pr : pairs) { dp.u[dp.n] = pr.first; dp.v[dp.n] = pr.second; ++dp.n; }
+    prof_begin(p, "vec_dots", 32.0 * dp.n * B.N, 0.0, st());
     k_dots<<<G(), kRedThreads, 0, st()>>>(dp, B.N, p->partials);
+    prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
     chk(launch_finalize(p, dp.n, G(), dst, st()));
   }
   void lincomb(double2* out, const double2* v0, Coef c0, const double2* v1, Coef c1, const double2* v2, Coef c2,
                const double2* w, int dst, const int* pred = nullptr) {
+    const double nv = (v0 ? 1 : 0) + (v1 ? 1 : 0) + (v2 ? 1 : 0) + (w ? 1 : 0) + 1;
+    prof_begin(p, "vec_lincomb", 16.0 * nv * B.N, 0.0, st());
     k_lincomb<<<G(), kRedThreads, 0, st()>>>(out, v0, c0, v1, c1, v2, c2, w, B.N, p->partials, pred);
+    prof_end(p, st());
     k_finalize<<<2, kRedThreads, 0, st()>>>(p->partials, G(), p->scal + dst, pred);
     count_launches(2);
     chk(cudaGetLastError());
@@ -498,12 +538,16 @@ struct Seq {
     lincomb(phin, B.phi[q], Coef{&c()->cr, 1.0}, B.p[q], Coef{&c()->sr, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr,
             S_T);
     ctl1(k_c_norm, c(), s());
+    prof_begin(p, "vec_scale_linf", 48.0 * B.N, 0.0, st());
     k_scale_linf<<<G(), kRedThreads, 0, st()>>>(phin, B.phi[q], &c()->inv, B.N, p->partials);
+    prof_end(p, st());
     k_finalize_max<<<1, kRedThreads, 0, st()>>>(p->partials, G(), p->scal + S_L);
     count_launches(2);
     chk(cudaGetLastError());
     atkm(SRC_PSI, reinterpret_cast<const double*>(phin), nullptr, B.Phi[q ^ 1]);
+    prof_begin(p, "vec_quartic", 24.0 * B.N, 0.0, st());
     k_quartic_sums<<<G(), kRedThreads, 0, st()>>>(phin, B.Phi[q ^ 1], B.N, p->partials);
+    prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
     chk(launch_finalize(p, 2, G(), S_Q, st()));
@@ -520,9 +564,12 @@ struct Seq {
   void iteration() {
     top();
     chk(precond());
-    dots({{B.Pr, B.phi[q]}, {B.r[q], B.Pr}, {B.r[q], B.phi[q]}, {B.r[q ^ 1], B.Pr}, {B.r[q ^ 1], B.phi[q]},
-          {B.p[q ^ 1], B.phi[q]}, {B.phi[q], B.phi[q]}},
-         S_D);
+    prof_begin(p, "vec_dir_dots", 80.0 * B.N, 0.0, st());
+    k_dir_dots<<<G(), kRedThreads, 0, st()>>>(B.Pr, B.phi[q], B.r[q], B.r[q ^ 1], B.p[q ^ 1], B.N, p->partials);
+    prof_end(p, st());
+    count_launches(1);
+    chk(cudaGetLastError());
+    chk(launch_finalize(p, 7, G(), S_D, st()));
     ctl1(k_c_dir, c(), s());
     lincomb(B.p[q], B.Pr, Coef{&c()->cp0, 1.0}, B.p[q ^ 1], Coef{&c()->cp1, 1.0}, B.phi[q], Coef{&c()->cp2, 1.0},
             B.Hphi, S_P);
@@ -533,8 +580,10 @@ struct Seq {
     hop(B.p[q], B.Hp, -1);
     atkm(SRC_PAIR, reinterpret_cast<const double*>(B.phi[q]), reinterpret_cast<const double*>(B.p[q]), B.Phi1);
     dots({{B.Hp, B.p[q]}}, S_C);
+    prof_begin(p, "vec_curv_sums", 48.0 * B.N, 0.0, st());
     k_curv_sums<<<G(), kRedThreads, 0, st()>>>(B.phi[q], B.p[q], B.Phi[q], B.Phi1, ph.beta, ph.lambda, B.N,
                                                 p->partials);
+    prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
     chk(launch_finalize(p, 3, G(), S_C + 1, st()));
@@ -552,16 +601,24 @@ struct Seq {
 };
 
 // Runs a phase through its CUDA graph (captured on the second use) or eagerly.
+// With profiling on, the graph carries event-record nodes around each pass;
+// B.last then points at them so the caller can accumulate their times after
+// the replay has completed.
 static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   PcgBuffers& B = S.B;
+  atkm_plan* p = S.p;
   const int fi = S.f32 ? 1 : 0;
+  const bool prof = p->prof != nullptr;
+  B.last = nullptr;
   if (!use_graphs || !B.graphs_ok) {
     S.run(kind);
     return S.err;
   }
+  if (B.gx[fi][S.q][kind] && B.gprof[fi][S.q][kind] != prof) drop_graph(&B, fi, S.q, kind);
   cudaGraphExec_t& gx = B.gx[fi][S.q][kind];
   if (gx) {
     count_launches(B.gnodes[fi][S.q][kind]);
+    if (prof) B.last = &B.grecs[fi][S.q][kind];
     return cudaGraphLaunch(gx, B.st);
   }
   if (!B.seen[fi][S.q][kind]) {  // first use: run eagerly (prepares kernel attributes)
@@ -576,7 +633,9 @@ static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
     S.run(kind);
     return S.err;
   }
+  if (prof) prof_set_sink(p, &B.grecs[fi][S.q][kind]);
   S.run(kind);
+  if (prof) prof_set_sink(p, nullptr);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(B.st, &g);
   const int nodes = (int)(atkm_launch_count() - c0);
@@ -584,6 +643,7 @@ static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   if (S.err != cudaSuccess || e2 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
+    drop_graph(&B, fi, S.q, kind);
     B.graphs_ok = false;
     S.err = cudaSuccess;
     S.run(kind);
@@ -594,12 +654,15 @@ static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   if (e != cudaSuccess) {
     gx = nullptr;
     cudaGetLastError();
+    drop_graph(&B, fi, S.q, kind);
     B.graphs_ok = false;
     S.run(kind);
     return S.err;
   }
   B.gnodes[fi][S.q][kind] = nodes;
+  B.gprof[fi][S.q][kind] = prof;
   count_launches(nodes);
+  if (prof) B.last = &B.grecs[fi][S.q][kind];
   return cudaGraphLaunch(gx, B.st);
 }
 
@@ -660,7 +723,7 @@ struct Solver {
     if (B->gphys_set && memcmp(&B->gphys, &ph, sizeof(Phys)) != 0) destroy_graphs(B);
     B->gphys = ph;
     B->gphys_set = true;
-    use_graphs = (plan->prof == nullptr) && !opts->no_graphs;
+    use_graphs = !opts->no_graphs;
     began = true;
     chk(cudaEventRecord(B->ev_in, caller));  // order after the caller's prior work
     chk(cudaStreamWaitEvent(B->st, B->ev_in, 0));
@@ -713,7 +776,13 @@ struct Solver {
     fetch_async();
   }
 
-  void wait() { chk(cudaStreamSynchronize(B->st)); }
+  void wait() {
+    chk(cudaStreamSynchronize(B->st));
+    if (B->last) {  // graph replay with profiling events: collect its pass times
+      prof_accumulate(plan, *B->last);
+      B->last = nullptr;
+    }
+  }
 
   void finish_iteration(bool accepted) {
     Ctl& h = H();

@@ -242,10 +242,17 @@ struct Profiler {
     double bytes, flops;
     cudaEvent_t a, b;
   };
-  std::vector<Rec> recs;
+  struct Agg {
+    const char* name;
+    long launches;
+    double ms, bytes, flops;
+  };
+  std::vector<Rec> recs;                // eager launches since profiling was enabled
+  std::vector<Agg> agg;                 // totals accumulated from graph replays
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   bool open = false;
+  std::vector<ProfRec>* sink = nullptr;  // graph capture in progress
   cudaEvent_t get() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -253,6 +260,14 @@ struct Profiler {
       pool.push_back(e);
     }
     return pool[used++];
+  }
+  void add(const char* name, double ms, double bytes, double flops) {
+    for (auto& a : agg)
+      if (strcmp(a.name, name) == 0) {
+        a.launches += 1; a.ms += ms; a.bytes += bytes; a.flops += flops;
+        return;
+      }
+    agg.push_back(Agg{name, 1, ms, bytes, flops});
   }
   ~Profiler() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
@@ -262,6 +277,19 @@ struct Profiler {
 void prof_begin(atkm_plan* p, const char* name, double bytes, double flops, cudaStream_t st) {
   Profiler* pr = p->prof;
   if (!pr) return;
+  if (pr->sink) {
+    ProfRec r{name, bytes, flops, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess) { cudaGetLastError(); return; }
+    // external event node: re-recorded on every replay of the captured graph
+    if (cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(r.a);
+      return;
+    }
+    pr->sink->push_back(r);
+    pr->open = true;
+    return;
+  }
   Profiler::Rec r{name, bytes, flops, pr->get(), nullptr};
   if (!r.a) return;
   cudaEventRecord(r.a, st);
@@ -273,10 +301,37 @@ void prof_end(atkm_plan* p, cudaStream_t st) {
   Profiler* pr = p->prof;
   if (!pr || !pr->open) return;
   pr->open = false;
+  if (pr->sink) {
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess) b = nullptr;
+    if (!b || cudaEventRecordWithFlags(b, st, cudaEventRecordExternal) != cudaSuccess) {
+      cudaGetLastError();
+      if (b) cudaEventDestroy(b);
+      pr->sink->back().b = nullptr;  // incomplete record: skipped when accumulating
+      return;
+    }
+    pr->sink->back().b = b;
+    return;
+  }
   cudaEvent_t b = pr->get();
   if (!b) { pr->recs.pop_back(); return; }
   cudaEventRecord(b, st);
   pr->recs.back().b = b;
+}
+
+void prof_set_sink(atkm_plan* p, std::vector<ProfRec>* sink) {
+  if (p->prof) p->prof->sink = sink;
+}
+
+void prof_accumulate(atkm_plan* p, const std::vector<ProfRec>& recs) {
+  Profiler* pr = p->prof;
+  if (!pr) return;
+  for (const auto& r : recs) {
+    if (!r.a || !r.b) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) pr->add(r.name, ms, r.bytes, r.flops);
+    else cudaGetLastError();  // do not leave the query's error for the next launch check
+  }
 }
 
 }  // namespace atkm
@@ -494,8 +549,10 @@ int atkm_plan_set_profiling(atkm_plan* plan, int on) {
     }
     cudaDeviceSynchronize();
     plan->prof->recs.clear();
+    plan->prof->agg.clear();
     plan->prof->used = 0;
     plan->prof->open = false;
+    plan->prof->sink = nullptr;
   } else if (plan->prof) {
     // keep the record for atkm_plan_kernel_stats; stop recording new launches
     delete plan->prof_stopped_;
@@ -516,7 +573,10 @@ int atkm_plan_kernel_stats(atkm_plan* plan, atkm_kernel_stat* out, int capacity,
   for (const auto& r : pr->recs) {
     if (!r.b) continue;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
     int k = -1;
     for (size_t i = 0; i < agg.size(); ++i)
       if (strncmp(agg[i].name, r.name, sizeof(agg[i].name)) == 0) k = (int)i;
@@ -531,6 +591,22 @@ int atkm_plan_kernel_stats(atkm_plan* plan, atkm_kernel_stat* out, int capacity,
     agg[k].ms_total += ms;
     agg[k].bytes_total += r.bytes;
     agg[k].flops_total += r.flops;
+  }
+  for (const auto& a : pr->agg) {
+    int k = -1;
+    for (size_t i = 0; i < agg.size(); ++i)
+      if (strncmp(agg[i].name, a.name, sizeof(agg[i].name)) == 0) k = (int)i;
+    if (k < 0) {
+      atkm_kernel_stat st;
+      memset(&st, 0, sizeof(st));
+      strncpy(st.name, a.name, sizeof(st.name) - 1);
+      agg.push_back(st);
+      k = (int)agg.size() - 1;
+    }
+    agg[k].launches += (int)a.launches;
+    agg[k].ms_total += a.ms;
+    agg[k].bytes_total += a.bytes;
+    agg[k].flops_total += a.flops;
   }
   *count = (int)agg.size();
   for (int i = 0; i < capacity && i < (int)agg.size(); ++i) out[i] = agg[i];

@@ -305,3 +305,22 @@ def test_batched_rejects_shared_plan(lib):
     b = a.clone()
     with pytest.raises(lib.AtkmError):
         lib.pcg_ground_state_batched([plan, plan], [prm, prm], [a, b], max_iter=2)
+
+
+def test_profiling_over_graph_replay(lib):
+    """Per-pass CUDA-event timing works on the captured-graph path and does
+    not change results."""
+    w = W.CONFIGS["cfg1_32x32x16"]
+    plan = lib.Plan(w.N, w.L, w.n, f32=True)
+    prm = lib.make_params(w.gamma, w.beta, w.lam, w.Omega)
+    ref = dev(W.initial_guess(w))
+    r0 = plan.pcg_ground_state(prm, ref, max_iter=6, precision=1)
+    psi = dev(W.initial_guess(w))
+    plan.set_profiling(True)
+    r1 = plan.pcg_ground_state(prm, psi, max_iter=6, precision=1)
+    stats = {s["name"]: s for s in plan.kernel_stats()}
+    plan.set_profiling(False)
+    assert np.array_equal(host(psi), host(ref)) and r0["E"] == r1["E"]
+    z = stats["atkm_z_f32"]
+    assert z["launches"] >= 12 and z["ms_total"] > 0 and z["bytes_total"] > 0
+    assert stats["H_x_f32"]["launches"] >= 6
