@@ -209,3 +209,32 @@ def sweep_instances(count: int = 48, seed: int = 4):
         out.append(Workload(f"sweep{i:02d}_{e}x{e}x{e // 4}", (e, e, e // 4), (16.0, 16.0, Lz),
                             (1.0, 1.0, gz), 200.0, 200.0 * lr, (0.0, 0.0, 1.0), Om, "phi_d"))
     return out
+
+
+GUESS_COARSE_N = (64, 64, 16)
+GUESS_FINE_N = (128, 128, 32)
+
+
+def guess_draws(count: int, seed: int = 5, N=GUESS_COARSE_N):
+    """Seeded parameter draws of the learned-guess workload: Omega ~ U[0.3, 0.95],
+    gamma = (1, 1, gamma_z) with gamma_z ~ U[5, 50], beta ~ U[100, 1000],
+    lambda/beta ~ U[0, 0.45], dipole tilt
+    theta ~ U[0, 60 deg] in the xz plane (n = (sin theta, 0, cos theta)); box
+    [-16,16]^2 x [-sqrt(64/gamma_z), sqrt(64/gamma_z)]; initial guess (d)."""
+    g = SplitMix64(seed)
+    out = []
+    for i in range(count):
+        Om = 0.3 + 0.65 * g.uniform()
+        gz = 5.0 + 45.0 * g.uniform()
+        beta = 100.0 + 900.0 * g.uniform()
+        lr = 0.45 * g.uniform()
+        th = math.radians(60.0) * g.uniform()
+        Lz = math.sqrt(64.0 / gz)
+        out.append(Workload(f"guess{seed}_{i:04d}", tuple(N), (16.0, 16.0, Lz), (1.0, 1.0, gz), beta, lr * beta,
+                            (math.sin(th), 0.0, math.cos(th)), Om, "phi_d", seed=i))
+    return out
+
+
+def with_grid(w: Workload, N) -> Workload:
+    """The same problem on another grid of the same box."""
+    return Workload(w.name, tuple(N), w.L, w.gamma, w.beta, w.lam, w.n, w.Omega, w.guess, w.seed, dict(w.extra))

@@ -255,6 +255,49 @@ int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_para
                              void* stream);
 
 /*
+ * atkm_spectral_upsample -- psi_f = the Fourier interpolant of psi_c
+ * (Eq. (Fourphi): sum over k in Lambda_Nc of coef_k W_k) evaluated on the fine
+ * plan's grid; the interpolation step of the cascadic multigrid driver
+ * (Algorithm 2, Step 2) and of the learned guess.  Both plans must have the
+ * same box; the fine grid may not be coarser on any axis.  psi_c: coarse N_c
+ * complex (device), psi_f: fine N_f complex (device, output; must not alias).
+ * Uses the coarse plan's T1 workspace.  Stream-ordered.
+ */
+int atkm_spectral_upsample(atkm_plan* coarse, atkm_plan* fine, const double* psi_c, double* psi_f,
+                           void* stream);
+
+/*
+ * Learned initial guess.  The paper chooses psi_0 among fixed formulas (§3,
+ * ten initial guesses) or interpolates a coarse solution (Algorithm 2); this
+ * network maps the 8 workload features (Omega, gamma_x, gamma_y, ln gamma_z,
+ * ln beta, lambda/beta, sin theta, cos theta of n = (sin theta, 0, cos theta))
+ * to psi_0 on a 16x64x64 (z, y, x) grid: MLP 8 -> 256 (ReLU) -> 8192 = latent
+ * 4x8x8 voxels x 32 channels -> transposed 3D convolutions with kernel =
+ * stride: 32 -> 16 ch (stride 2, ReLU), 16 -> 8 (stride 2, ReLU), 8 -> 2
+ * (stride (1,2,2); Re, Im).  Every layer runs as a GEMM with BF16 operands
+ * and FP32 accumulation on the tensor cores; parameters are FP32 (master
+ * copy) and trained with Adam on the loss 1 - |<u,t>|^2/(|u|^2 |t|^2) (mean
+ * over the batch), which ignores the global phase and scale of the targets.
+ *   feats    device, batch x 8 floats.
+ *   psi      device, batch x 16 x 64 x 64 complex doubles (forward output).
+ *   targets  device, batch x 16 x 64 x 64 complex doubles.
+ *   grad_out device, atkm_guess_net_num_params() floats (may be NULL).
+ *   loss     device, 1 float (batch mean).
+ * Parameters are one flat float vector (get/set copy it device to device).
+ */
+typedef struct atkm_guess_net atkm_guess_net;
+unsigned long long atkm_guess_net_num_params(void);
+int atkm_guess_net_create(atkm_guess_net** out, unsigned long long seed, void* stream);
+void atkm_guess_net_destroy(atkm_guess_net* net);
+int atkm_guess_net_get_params(const atkm_guess_net* net, float* dst, void* stream);
+int atkm_guess_net_set_params(atkm_guess_net* net, const float* src, void* stream);
+int atkm_guess_net_forward(atkm_guess_net* net, int batch, const float* feats, double* psi, void* stream);
+int atkm_guess_net_grad(atkm_guess_net* net, int batch, const float* feats, const double* targets,
+                        float* grad_out, float* loss, void* stream);
+int atkm_guess_net_train_step(atkm_guess_net* net, int batch, const float* feats, const double* targets,
+                              float lr, float* loss, void* stream);
+
+/*
  * atkm_inner_products_noalloc -- out[i] = hvol * Re(sum_j u_i[j] conj(v_i[j]))
  * for i < npairs, without allocating anything.  The paper has no counterpart:
  * this is for callers that cannot call cudaMalloc (code inside a host

@@ -98,6 +98,15 @@ def load_library(path: str = LIB_PATH):
         "pcg_ground_state": (ip, [vp, C.POINTER(Params), C.POINTER(PcgOpts), vp, C.POINTER(Result), vp]),
         "pcg_ground_state_batched": (ip, [C.c_int, C.POINTER(vp), C.POINTER(Params), C.POINTER(PcgOpts),
                                           C.POINTER(vp), C.POINTER(Result), vp]),
+        "atkm_spectral_upsample": (ip, [vp, vp, vp, vp, vp]),
+        "atkm_guess_net_num_params": (C.c_ulonglong, []),
+        "atkm_guess_net_create": (ip, [C.POINTER(vp), C.c_ulonglong, vp]),
+        "atkm_guess_net_destroy": (None, [vp]),
+        "atkm_guess_net_get_params": (ip, [vp, vp, vp]),
+        "atkm_guess_net_set_params": (ip, [vp, vp, vp]),
+        "atkm_guess_net_forward": (ip, [vp, C.c_int, vp, vp, vp]),
+        "atkm_guess_net_grad": (ip, [vp, C.c_int, vp, vp, vp, vp, vp]),
+        "atkm_guess_net_train_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, vp]),
         "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
         "atkm_launch_count": (C.c_ulonglong, []),
         "atkm_inner_products_noalloc": (ip, [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_ulonglong, C.c_double, vp,
@@ -158,6 +167,83 @@ def inner_products_noalloc(us, vs, hvol: float, out: torch.Tensor, stream=None) 
     if code != ATKM_OK:
         raise AtkmError(code, lib.atkm_last_error_string(None).decode())
     return out
+
+
+def spectral_upsample(coarse: "Plan", fine: "Plan", psi_c: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """Fourier interpolant of psi_c on the fine plan's grid (same box)."""
+    lib = load_library()
+    out = torch.empty(fine.shape, dtype=torch.complex128, device="cuda") if out is None else out
+    code = lib.atkm_spectral_upsample(coarse._h, fine._h, _ptr(psi_c, torch.complex128, coarse.shape, "psi_c"),
+                                      _ptr(out, torch.complex128, fine.shape, "psi_f"), _stream(stream))
+    if code != ATKM_OK:
+        raise AtkmError(code, lib.atkm_last_error_string(None).decode())
+    return out
+
+
+GUESS_SHAPE = (16, 64, 64)
+
+
+class GuessNet:
+    """Handle of the learned initial-guess network (see include/atkm.h)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        self._lib = load_library()
+        self._h = C.c_void_p()
+        code = self._lib.atkm_guess_net_create(C.byref(self._h), int(seed), _stream(stream))
+        if code != ATKM_OK:
+            raise AtkmError(code, self._lib.atkm_last_error_string(None).decode())
+        self.num_params = int(self._lib.atkm_guess_net_num_params())
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                self._lib.atkm_guess_net_destroy(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    def _check(self, code):
+        if code != ATKM_OK:
+            raise AtkmError(code, self._lib.atkm_last_error_string(None).decode())
+
+    def get_params(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        self._check(self._lib.atkm_guess_net_get_params(self._h, C.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def set_params(self, w: torch.Tensor, stream=None):
+        _ptr(w, torch.float32, (self.num_params,), "params")
+        self._check(self._lib.atkm_guess_net_set_params(self._h, C.c_void_p(w.data_ptr()), _stream(stream)))
+
+    def forward(self, feats: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        B = feats.shape[0]
+        _ptr(feats, torch.float32, (B, 8), "feats")
+        out = torch.empty((B,) + GUESS_SHAPE, dtype=torch.complex128, device="cuda") if out is None else out
+        _ptr(out, torch.complex128, (B,) + GUESS_SHAPE, "psi")
+        self._check(self._lib.atkm_guess_net_forward(self._h, B, C.c_void_p(feats.data_ptr()),
+                                                     C.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def grad(self, feats: torch.Tensor, targets: torch.Tensor, stream=None):
+        B = feats.shape[0]
+        _ptr(feats, torch.float32, (B, 8), "feats")
+        _ptr(targets, torch.complex128, (B,) + GUESS_SHAPE, "targets")
+        g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        self._check(self._lib.atkm_guess_net_grad(self._h, B, C.c_void_p(feats.data_ptr()),
+                                                  C.c_void_p(targets.data_ptr()), C.c_void_p(g.data_ptr()),
+                                                  C.c_void_p(loss.data_ptr()), _stream(stream)))
+        return g, loss
+
+    def train_step(self, feats: torch.Tensor, targets: torch.Tensor, lr: float, loss=None, stream=None):
+        B = feats.shape[0]
+        _ptr(feats, torch.float32, (B, 8), "feats")
+        _ptr(targets, torch.complex128, (B,) + GUESS_SHAPE, "targets")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda") if loss is None else loss
+        self._check(self._lib.atkm_guess_net_train_step(self._h, B, C.c_void_p(feats.data_ptr()),
+                                                        C.c_void_p(targets.data_ptr()), C.c_float(lr),
+                                                        C.c_void_p(loss.data_ptr()), _stream(stream)))
+        return loss
 
 
 def launch_count() -> int:

@@ -326,6 +326,8 @@ template <typename R>
 cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev, const double* r,
                            const double* phi, const double* Phi, double* Pr, cudaStream_t st);
 
+template <typename R> cudaError_t launch_cfft3(atkm_plan* p, cx<R>* buf, int sign, cudaStream_t st);
+
 // Reductions (pcg.cu)
 cudaError_t launch_finalize(atkm_plan* p, int nslots, int nblocks, int dst_slot, cudaStream_t st);
 

@@ -1,0 +1,560 @@
+// Learned initial guess: parameters of the workload -> psi_0 on a 16x64x64 grid.
+//
+// Network: features f (8) -> h1 = relu(f W1 + b1) (256) -> z = h1 W2 + b2
+// (8192 = latent 4x8x8 voxels x 32 channels) -> three transposed 3D
+// convolutions whose kernel equals their stride (so each is a per-voxel
+// linear map followed by a pixel shuffle):
+//   L1: 32 ch -> 16 ch, stride (2,2,2), relu;   L2: 16 -> 8, stride (2,2,2), relu;
+//   L3: 8 -> 2 (Re, Im), stride (1,2,2).
+// Activations stay in GEMM row order (row = voxel, column = sub-position x
+// channel); only the final output is mapped to the (z, y, x) grid.  Every
+// layer is a GEMM with BF16 operands and FP32 accumulation on the tensor cores
+// (warp-level mma m16n8k16); weights have FP32 master copies updated by Adam.
+// Loss per sample (phase and scale invariant, so targets defined up to a
+// global phase are learnable): L = 1 - |<u,t>|^2 / (|u|^2 |t|^2).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "atkm_internal.cuh"
+
+namespace atkm {
+namespace {
+
+// ------------------------------------------------------------- shapes
+constexpr int kF = 8, kFpad = 16, kH = 256, kZ = 8192, kC0 = 32, kV0 = 256;  // latent 4x8x8 voxels
+constexpr int kC1 = 16, kC2 = 8, kC3 = 2;
+constexpr int kN1 = 8 * kC1, kN2 = 8 * kC2, kN3 = 4 * kC3;  // GEMM output widths of L1..L3
+constexpr int kOutZ = 16, kOutY = 64, kOutX = 64, kOutN = kOutZ * kOutY * kOutX;
+
+// Parameter offsets in the flat FP32 vector.
+struct Layout {
+  size_t W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, total;
+};
+constexpr Layout make_layout() {
+  Layout l{};
+  size_t o = 0;
+  l.W1 = o; o += (size_t)kFpad * kH;
+  l.b1 = o; o += kH;
+  l.W2 = o; o += (size_t)kH * kZ;
+  l.b2 = o; o += kZ;
+  l.W3 = o; o += (size_t)kC0 * kN1;
+  l.b3 = o; o += kC1;
+  l.W4 = o; o += (size_t)kC1 * kN2;
+  l.b4 = o; o += kC2;
+  l.W5 = o; o += (size_t)kC2 * kN3;
+  l.b5 = o; o += kC3;
+  l.total = o;
+  return l;
+}
+constexpr Layout kL = make_layout();
+
+// ------------------------------------------------------------- GEMM
+// C[M x N] (+)= A[M x K] * B[K x N]; A(m,k) = A[m*sam + k*sak],
+// B(k,n) = B[k*sbk + n*sbn], C(m,n) = C[m*ldc + n] (FP32 everywhere in
+// memory).  Operands are rounded to BF16 when staged into shared memory;
+// products accumulate in FP32 on the tensor cores.  gridDim.z splits K; with
+// more than one split the partial tiles are added atomically into C (which the
+// caller zeroes).  CTA tile 64x64, 4 warps of 32x32, K step 16.
+constexpr int kTM = 64, kTN = 64, kTK = 16, kGemmThreads = 128;
+
+__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(kGemmThreads)
+k_gemm_bf16(const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbk, long sbn,
+            float* __restrict__ C, int ldc, int M, int N, int K, int kchunk) {
+  __shared__ __nv_bfloat16 As[kTM][kTK + 8];
+  __shared__ __nv_bfloat16 Bs[kTN][kTK + 8];
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, tq = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += kTK) {
+    for (int e = threadIdx.x; e < kTM * kTK; e += kGemmThreads) {
+      const int mm = e / kTK, kk = e % kTK;
+      const int m = m0 + mm, k = k0 + kk;
+      const float v = (m < M && k < ke) ? A[(long)m * sam + (long)k * sak] : 0.f;
+      As[mm][kk] = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < kTN * kTK; e += kGemmThreads) {
+      const int nn = e / kTK, kk = e % kTK;
+      const int n = n0 + nn, k = k0 + kk;
+      const float v = (n < N && k < ke) ? Bm[(long)k * sbk + (long)n * sbn] : 0.f;
+      Bs[nn][kk] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+    unsigned a[2][4], b[4][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = wm + 16 * i + g;
+      a[i][0] = pack_bf16(As[r][2 * tq], As[r][2 * tq + 1]);
+      a[i][1] = pack_bf16(As[r + 8][2 * tq], As[r + 8][2 * tq + 1]);
+      a[i][2] = pack_bf16(As[r][2 * tq + 8], As[r][2 * tq + 9]);
+      a[i][3] = pack_bf16(As[r + 8][2 * tq + 8], As[r + 8][2 * tq + 9]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = wn + 8 * j + g;
+      b[j][0] = pack_bf16(Bs[c][2 * tq], Bs[c][2 * tq + 1]);
+      b[j][1] = pack_bf16(Bs[c][2 * tq + 8], Bs[c][2 * tq + 9]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+            : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    __syncthreads();
+  }
+  const bool split = gridDim.z > 1;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + 16 * i + g + ((r >= 2) ? 8 : 0);
+        const int n = n0 + wn + 8 * j + 2 * tq + (r & 1);
+        if (m < M && n < N) {
+          float* dst = C + (long)m * ldc + n;
+          if (split) atomicAdd(dst, acc[i][j][r]);
+          else *dst = acc[i][j][r];
+        }
+      }
+}
+
+// ------------------------------------------------------------- elementwise
+// y = act(x + b[col % cb]) in place (act = relu when relu != 0).
+__global__ void k_bias_act(float* __restrict__ x, const float* __restrict__ b, long rows, int cols, int cb, int relu) {
+  const long total = rows * cols;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    float v = x[i] + b[(int)(i % cols) % cb];
+    x[i] = (relu && v < 0.f) ? 0.f : v;
+  }
+}
+
+// dx *= (y > 0)
+__global__ void k_relu_back(float* __restrict__ dx, const float* __restrict__ y, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (!(y[i] > 0.f)) dx[i] = 0.f;
+}
+
+// db[c] += sum over rows and over the column groups of dy[.., g*cb + c]
+__global__ void k_bias_grad(const float* __restrict__ dy, float* __restrict__ db, long rows, int cols, int cb) {
+  __shared__ float sh[256];
+  const int c = blockIdx.x;  // output channel
+  float acc = 0.f;
+  const long total = rows * (cols / cb);
+  for (long i = blockIdx.y * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.y * blockDim.x) {
+    const long row = i / (cols / cb);
+    const int grp = (int)(i % (cols / cb));
+    acc += dy[row * cols + grp * cb + c];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&db[c], sh[0]);
+}
+
+// Features padded to 16 columns (the tensor-core K step).
+__global__ void k_pad_features(const float* __restrict__ f, float* __restrict__ fp, int B) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * kFpad; i += gridDim.x * blockDim.x) {
+    const int b = i / kFpad, c = i % kFpad;
+    fp[i] = c < kF ? f[b * kF + c] : 0.f;
+  }
+}
+
+// Grid position of element (row, col) of the L3 output.
+// row = ((b*256 + v0)*8 + s1)*8 + s2, col = s3*2 + ch; v0 = (iz,iy,ix) in
+// 4x8x8, s1 = (a1,b1,c1), s2 = (a2,b2,c2) in {0,1}^3, s3 = (b3,c3) in {0,1}^2.
+__device__ __forceinline__ void out_pos(long row, int col, int& b, int& z, int& y, int& x, int& ch) {
+  const int s2 = (int)(row & 7);
+  const int s1 = (int)((row >> 3) & 7);
+  const long r0 = row >> 6;
+  const int v0 = (int)(r0 % kV0);
+  b = (int)(r0 / kV0);
+  const int iz = v0 >> 6, iy = (v0 >> 3) & 7, ix = v0 & 7;
+  ch = col & 1;
+  const int s3 = col >> 1;
+  z = (iz * 2 + (s1 >> 2)) * 2 + (s2 >> 2);
+  y = ((iy * 2 + ((s1 >> 1) & 1)) * 2 + ((s2 >> 1) & 1)) * 2 + (s3 >> 1);
+  x = ((ix * 2 + (s1 & 1)) * 2 + (s2 & 1)) * 2 + (s3 & 1);
+}
+
+// L3 output -> psi (B x 16 x 64 x 64 complex, FP64)
+__global__ void k_out_to_psi(const float* __restrict__ o, double* __restrict__ psi, int B) {
+  const long total = (long)B * kOutN * 2;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long row = i / kN3;
+    const int col = (int)(i % kN3);
+    int b, z, y, x, ch;
+    out_pos(row, col, b, z, y, x, ch);
+    psi[(((long)b * kOutZ + z) * kOutY + y) * kOutX * 2 + (long)x * 2 + ch] = (double)o[i];
+  }
+}
+
+// Per-sample sums for the loss: s = <u, t> (complex), uu = |u|^2, tt = |t|^2.
+// One block per sample; u is read from the L3 output, t from FP64 targets.
+__global__ void k_loss_sums(const float* __restrict__ o, const double* __restrict__ t, double* __restrict__ sums) {
+  __shared__ double sh[4][256];
+  const int b = blockIdx.x;
+  double a[4] = {0, 0, 0, 0};
+  const long base = (long)b * kOutN * 2;
+  for (long i = threadIdx.x; i < (long)kOutN; i += blockDim.x) {
+    // iterate over grid points via output rows: element pairs (ch 0, ch 1)
+    const long e = base + 2 * i;             // index into o of (row, 2*s3)
+    const long row = e / kN3;
+    const int col = (int)(e % kN3);
+    int bb, z, y, x, ch;
+    out_pos(row, col, bb, z, y, x, ch);
+    const double ur = o[e], ui = o[e + 1];
+    const long ti = (((long)b * kOutZ + z) * kOutY + y) * kOutX + x;
+    const double tr = t[2 * ti], tim = t[2 * ti + 1];
+    a[0] += ur * tr + ui * tim;   // Re <u,t> = Re sum u conj(t)
+    a[1] += ui * tr - ur * tim;   // Im
+    a[2] += ur * ur + ui * ui;
+    a[3] += tr * tr + tim * tim;
+  }
+  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = a[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) sums[b * 4 + k] = sh[k][0];
+}
+
+// Loss (mean over the batch) and dL/d(Re u, Im u) in the L3 output layout:
+// g = -2 (s t / (uu tt) - |s|^2 u / (uu^2 tt)) / B.
+__global__ void k_loss_grad(const float* __restrict__ o, const double* __restrict__ t, const double* __restrict__ sums,
+                            float* __restrict__ dO, float* __restrict__ loss, int B) {
+  const long total = (long)B * kOutN;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long e = 2 * i;
+    const long row = e / kN3;
+    const int col = (int)(e % kN3);
+    int b, z, y, x, ch;
+    out_pos(row, col, b, z, y, x, ch);
+    const double sr = sums[b * 4 + 0], si = sums[b * 4 + 1], uu = sums[b * 4 + 2], tt = sums[b * 4 + 3];
+    const double s2 = sr * sr + si * si;
+    const long ti = (((long)b * kOutZ + z) * kOutY + y) * kOutX + x;
+    const double tr = t[2 * ti], tim = t[2 * ti + 1];
+    const double ur = o[e], ui = o[e + 1];
+    // s t = (sr + i si)(tr + i tim)
+    const double str = sr * tr - si * tim, sti = sr * tim + si * tr;
+    const double c1 = 1.0 / (uu * tt), c2 = s2 / (uu * uu * tt);
+    const double scale = -2.0 / B;
+    dO[e] = (float)(scale * (c1 * str - c2 * ur));
+    dO[e + 1] = (float)(scale * (c1 * sti - c2 * ui));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int b = 0; b < B; ++b) {
+      const double sr = sums[b * 4], si = sums[b * 4 + 1], uu = sums[b * 4 + 2], tt = sums[b * 4 + 3];
+      acc += 1.0 - (sr * sr + si * si) / (uu * tt);
+    }
+    *loss = (float)(acc / B);
+  }
+}
+
+// Adam (Kingma & Ba 2015) with bias correction.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// Deterministic initialisation (SplitMix64 -> uniform(-a, a), a = sqrt(3/fan_in))
+__device__ __forceinline__ unsigned long long smix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__global__ void k_init_uniform(float* __restrict__ w, long n, float a, unsigned long long seed) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double u = (double)(smix(seed + (unsigned long long)i) >> 11) * (1.0 / 9007199254740992.0);
+    w[i] = (float)((2.0 * u - 1.0) * a);
+  }
+}
+
+int ew_grid(long n) {
+  long b = (n + 255) / 256;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+}  // namespace atkm
+
+using namespace atkm;
+
+struct atkm_guess_net {
+  float* w = nullptr;   // FP32 master parameters
+  float* g = nullptr;   // gradients
+  float* m = nullptr;   // Adam moments
+  float* v = nullptr;
+  long step = 0;
+  int cap = 0;          // batch capacity of the activation buffers
+  float *fpad = nullptr, *h1 = nullptr, *z = nullptr, *y1 = nullptr, *y2 = nullptr, *o = nullptr;
+  float *dh1 = nullptr, *dz = nullptr, *dy1 = nullptr, *dy2 = nullptr, *dO = nullptr;
+  double* sums = nullptr;
+  std::string err;
+};
+
+namespace {
+
+void net_free_acts(atkm_guess_net* n) {
+  float* f[] = {n->fpad, n->h1, n->z, n->y1, n->y2, n->o, n->dh1, n->dz, n->dy1, n->dy2, n->dO};
+  for (float* p : f)
+    if (p) cudaFree(p);
+  if (n->sums) cudaFree(n->sums);
+  n->fpad = n->h1 = n->z = n->y1 = n->y2 = n->o = n->dh1 = n->dz = n->dy1 = n->dy2 = n->dO = nullptr;
+  n->sums = nullptr;
+  n->cap = 0;
+}
+
+cudaError_t net_ensure(atkm_guess_net* n, int B) {
+  if (B <= n->cap) return cudaSuccess;
+  net_free_acts(n);
+  cudaError_t e = cudaSuccess;
+  auto al = [&](float** p, size_t count) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, count * sizeof(float));
+  };
+  al(&n->fpad, (size_t)B * kFpad);
+  al(&n->h1, (size_t)B * kH);
+  al(&n->z, (size_t)B * kZ);
+  al(&n->y1, (size_t)B * kV0 * kN1);
+  al(&n->y2, (size_t)B * kV0 * 8 * kN2);
+  al(&n->o, (size_t)B * kV0 * 64 * kN3);
+  al(&n->dh1, (size_t)B * kH);
+  al(&n->dz, (size_t)B * kZ);
+  al(&n->dy1, (size_t)B * kV0 * kN1);
+  al(&n->dy2, (size_t)B * kV0 * 8 * kN2);
+  al(&n->dO, (size_t)B * kV0 * 64 * kN3);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->sums, (size_t)B * 4 * sizeof(double));
+  if (e != cudaSuccess) {
+    net_free_acts(n);
+    return e;
+  }
+  n->cap = B;
+  return cudaSuccess;
+}
+
+// C (+)= A(M x K) B(K x N) with the given strides; zeroes C first when split.
+cudaError_t gemm(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc, int M, int N,
+                 int K, cudaStream_t st, bool split_k) {
+  int splits = 1;
+  const int tiles = ((M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
+  if (split_k && tiles < 152) {
+    splits = (152 * 4) / tiles;
+    const int maxs = (K + kTK - 1) / kTK;
+    if (splits > maxs) splits = maxs;
+    if (splits < 1) splits = 1;
+  }
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + kTK - 1) / kTK * kTK;
+  splits = (K + kchunk - 1) / kchunk;
+  if (splits > 1) {
+    cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * ldc * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, splits);
+  k_gemm_bf16<<<grid, kGemmThreads, 0, st>>>(A, sam, sak, Bm, sbk, sbn, C, ldc, M, N, K, kchunk);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Forward pass for B samples (features fp[B x 16] already padded).
+cudaError_t net_forward(atkm_guess_net* n, int B, cudaStream_t st) {
+  const float* w = n->w;
+  cudaError_t e;
+  const long r1 = (long)B * kV0, r2 = r1 * 8, r3 = r2 * 8;
+  if ((e = gemm(n->fpad, kFpad, 1, w + kL.W1, kH, 1, n->h1, kH, B, kH, kFpad, st, false))) return e;
+  k_bias_act<<<ew_grid((long)B * kH), 256, 0, st>>>(n->h1, w + kL.b1, B, kH, kH, 1);
+  if ((e = gemm(n->h1, kH, 1, w + kL.W2, kZ, 1, n->z, kZ, B, kZ, kH, st, false))) return e;
+  k_bias_act<<<ew_grid((long)B * kZ), 256, 0, st>>>(n->z, w + kL.b2, B, kZ, kZ, 0);
+  if ((e = gemm(n->z, kC0, 1, w + kL.W3, kN1, 1, n->y1, kN1, (int)r1, kN1, kC0, st, false))) return e;
+  k_bias_act<<<ew_grid(r1 * kN1), 256, 0, st>>>(n->y1, w + kL.b3, r1, kN1, kC1, 1);
+  if ((e = gemm(n->y1, kC1, 1, w + kL.W4, kN2, 1, n->y2, kN2, (int)r2, kN2, kC1, st, false))) return e;
+  k_bias_act<<<ew_grid(r2 * kN2), 256, 0, st>>>(n->y2, w + kL.b4, r2, kN2, kC2, 1);
+  if ((e = gemm(n->y2, kC2, 1, w + kL.W5, kN3, 1, n->o, kN3, (int)r3, kN3, kC2, st, false))) return e;
+  k_bias_act<<<ew_grid(r3 * kN3), 256, 0, st>>>(n->o, w + kL.b5, r3, kN3, kC3, 0);
+  count_launches(5);
+  return cudaGetLastError();
+}
+
+// Gradient of the batch loss into n->g (overwritten); loss to *loss_dev.
+cudaError_t net_backward(atkm_guess_net* n, int B, const double* targets, float* loss_dev, cudaStream_t st) {
+  const float* w = n->w;
+  float* g = n->g;
+  cudaError_t e;
+  const long r1 = (long)B * kV0, r2 = r1 * 8, r3 = r2 * 8;
+  k_loss_sums<<<B, 256, 0, st>>>(n->o, targets, n->sums);
+  k_loss_grad<<<ew_grid((long)B * kOutN), 256, 0, st>>>(n->o, targets, n->sums, n->dO, loss_dev, B);
+  if ((e = cudaMemsetAsync(g, 0, kL.total * sizeof(float), st))) return e;
+  // L3
+  if ((e = gemm(n->y2, 1, kC2, n->dO, kN3, 1, g + kL.W5, kN3, kC2, kN3, (int)r3, st, true))) return e;
+  k_bias_grad<<<dim3(kC3, 64), 256, 0, st>>>(n->dO, g + kL.b5, r3, kN3, kC3);
+  if ((e = gemm(n->dO, kN3, 1, w + kL.W5, 1, kN3, n->dy2, kC2, (int)r3, kC2, kN3, st, false))) return e;
+  k_relu_back<<<ew_grid(r2 * kN2), 256, 0, st>>>(n->dy2, n->y2, r2 * kN2);
+  // L2
+  if ((e = gemm(n->y1, 1, kC1, n->dy2, kN2, 1, g + kL.W4, kN2, kC1, kN2, (int)r2, st, true))) return e;
+  k_bias_grad<<<dim3(kC2, 64), 256, 0, st>>>(n->dy2, g + kL.b4, r2, kN2, kC2);
+  if ((e = gemm(n->dy2, kN2, 1, w + kL.W4, 1, kN2, n->dy1, kC1, (int)r2, kC1, kN2, st, false))) return e;
+  k_relu_back<<<ew_grid(r1 * kN1), 256, 0, st>>>(n->dy1, n->y1, r1 * kN1);
+  // L1
+  if ((e = gemm(n->z, 1, kC0, n->dy1, kN1, 1, g + kL.W3, kN1, kC0, kN1, (int)r1, st, true))) return e;
+  k_bias_grad<<<dim3(kC1, 64), 256, 0, st>>>(n->dy1, g + kL.b3, r1, kN1, kC1);
+  if ((e = gemm(n->dy1, kN1, 1, w + kL.W3, 1, kN1, n->dz, kC0, (int)r1, kC0, kN1, st, false))) return e;
+  // MLP2 (no activation on z)
+  if ((e = gemm(n->h1, 1, kH, n->dz, kZ, 1, g + kL.W2, kZ, kH, kZ, B, st, true))) return e;
+  k_bias_grad<<<dim3(kZ, 1), 256, 0, st>>>(n->dz, g + kL.b2, B, kZ, kZ);
+  if ((e = gemm(n->dz, kZ, 1, w + kL.W2, 1, kZ, n->dh1, kH, B, kH, kZ, st, false))) return e;
+  k_relu_back<<<ew_grid((long)B * kH), 256, 0, st>>>(n->dh1, n->h1, (long)B * kH);
+  // MLP1
+  if ((e = gemm(n->fpad, 1, kFpad, n->dh1, kH, 1, g + kL.W1, kH, kFpad, kH, B, st, true))) return e;
+  k_bias_grad<<<dim3(kH, 1), 256, 0, st>>>(n->dh1, g + kL.b1, B, kH, kH);
+  count_launches(11);
+  return cudaGetLastError();
+}
+
+int net_fail(atkm_guess_net* n, int code, const std::string& m) {
+  if (n) n->err = m;
+  return fail(nullptr, code, m);
+}
+
+}  // namespace
+
+extern "C" {
+
+unsigned long long atkm_guess_net_num_params(void) { return (unsigned long long)kL.total; }
+
+int atkm_guess_net_create(atkm_guess_net** out, unsigned long long seed, void* stream) {
+  if (!out) return fail(nullptr, ATKM_ERR_ARG, "atkm_guess_net_create: out is NULL");
+  *out = nullptr;
+  atkm_guess_net* n = new atkm_guess_net();
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (float** p : {&n->w, &n->g, &n->m, &n->v})
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, kL.total * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->w, 0, kL.total * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, kL.total * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, kL.total * sizeof(float), st);
+  if (e == cudaSuccess) {
+    struct { size_t off; long count; int fan_in; } ws[] = {
+        {kL.W1, (long)kF * kH, kF}, {kL.W2, (long)kH * kZ, kH}, {kL.W3, (long)kC0 * kN1, kC0},
+        {kL.W4, (long)kC1 * kN2, kC1}, {kL.W5, (long)kC2 * kN3, kC2}};
+    for (int i = 0; i < 5; ++i) {
+      // W1 rows 8..15 (the padding) stay zero
+      k_init_uniform<<<ew_grid(ws[i].count), 256, 0, st>>>(n->w + ws[i].off, ws[i].count,
+                                                            (float)sqrt(3.0 / ws[i].fan_in), seed * 1000003ull + i);
+    }
+    count_launches(5);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    atkm_guess_net_destroy(n);
+    return cuda_fail(nullptr, e, "atkm_guess_net_create");
+  }
+  *out = n;
+  return ATKM_OK;
+}
+
+void atkm_guess_net_destroy(atkm_guess_net* n) {
+  if (!n) return;
+  cudaDeviceSynchronize();
+  net_free_acts(n);
+  for (float* p : {n->w, n->g, n->m, n->v})
+    if (p) cudaFree(p);
+  delete n;
+}
+
+int atkm_guess_net_get_params(const atkm_guess_net* n, float* dst, void* stream) {
+  if (!n || !dst) return fail(nullptr, ATKM_ERR_ARG, "atkm_guess_net_get_params: NULL argument");
+  cudaError_t e = cudaMemcpyAsync(dst, n->w, kL.total * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_get_params");
+}
+
+int atkm_guess_net_set_params(atkm_guess_net* n, const float* src, void* stream) {
+  if (!n || !src) return fail(nullptr, ATKM_ERR_ARG, "atkm_guess_net_set_params: NULL argument");
+  cudaError_t e = cudaMemcpyAsync(n->w, src, kL.total * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_set_params");
+}
+
+int atkm_guess_net_forward(atkm_guess_net* n, int batch, const float* feats, double* psi, void* stream) {
+  if (!n || !feats || !psi || batch < 1) return net_fail(n, ATKM_ERR_ARG, "atkm_guess_net_forward: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = net_ensure(n, batch);
+  if (e == cudaSuccess) {
+    k_pad_features<<<ew_grid((long)batch * kFpad), 256, 0, st>>>(feats, n->fpad, batch);
+    count_launches(1);
+    e = net_forward(n, batch, st);
+  }
+  if (e == cudaSuccess) {
+    k_out_to_psi<<<ew_grid((long)batch * kOutN * 2), 256, 0, st>>>(n->o, psi, batch);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_forward");
+}
+
+int atkm_guess_net_grad(atkm_guess_net* n, int batch, const float* feats, const double* targets, float* grad_out,
+                        float* loss, void* stream) {
+  if (!n || !feats || !targets || !loss || batch < 1) return net_fail(n, ATKM_ERR_ARG, "atkm_guess_net_grad: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = net_ensure(n, batch);
+  if (e == cudaSuccess) {
+    k_pad_features<<<ew_grid((long)batch * kFpad), 256, 0, st>>>(feats, n->fpad, batch);
+    count_launches(1);
+    e = net_forward(n, batch, st);
+  }
+  if (e == cudaSuccess) e = net_backward(n, batch, targets, loss, st);
+  if (e == cudaSuccess && grad_out)
+    e = cudaMemcpyAsync(grad_out, n->g, kL.total * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_grad");
+}
+
+int atkm_guess_net_train_step(atkm_guess_net* n, int batch, const float* feats, const double* targets, float lr,
+                              float* loss, void* stream) {
+  int code = atkm_guess_net_grad(n, batch, feats, targets, nullptr, loss, stream);
+  if (code != ATKM_OK) return code;
+  cudaStream_t st = (cudaStream_t)stream;
+  n->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
+  k_adam<<<ew_grid((long)kL.total), 256, 0, st>>>(n->w, n->g, n->m, n->v, (long)kL.total, lr, b1, b2, 1e-8f, c1, c2);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_train_step");
+}
+
+}  // extern "C"

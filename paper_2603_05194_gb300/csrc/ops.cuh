@@ -630,4 +630,20 @@ template <typename R> struct OpPXI : OpBase<1, false, 0, true> {
   }
 };
 
+// ---- in-place 3D complex FFT on a plan's (unpadded) grid, sign S.
+template <typename R, int S> struct OpCX : OpBase<S, false, 0, true> {
+  cx<R>* buf; Cst<R> c;
+  __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
+  __device__ cx<R> load(int o, int, int pos) const { return buf[(size_t)o * c.Nx + pos]; }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int, int pos, cx<R> v, R*) const { buf[(size_t)o * c.Nx + pos] = v; }
+};
+template <typename R, int S> struct OpCZ : OpBase<S, false, 0, false> {
+  cx<R>* buf; Cst<R> c;
+  __device__ bool valid(int, int x) const { return x < c.Nx; }
+  __device__ cx<R> load(int o, int x, int pos) const { return buf[((size_t)pos * c.Ny + o) * c.Nx + x]; }
+  __device__ void spectral(int, int, int, cx<R>&, R*) const {}
+  __device__ void store(int o, int x, int pos, cx<R> v, R*) const { buf[((size_t)pos * c.Ny + o) * c.Nx + x] = v; }
+};
+
 }  // namespace atkm

@@ -7,4 +7,5 @@ template cudaError_t launch_H<double>(atkm_plan*, const Phys&, const double*, co
                                       int, cudaStream_t);
 template cudaError_t launch_precond<double>(atkm_plan*, const Phys&, const double*, const double*, const double*,
                                             const double*, double*, cudaStream_t);
+template cudaError_t launch_cfft3<double>(atkm_plan*, double2*, int, cudaStream_t);
 }  // namespace atkm

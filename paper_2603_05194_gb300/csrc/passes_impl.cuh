@@ -191,6 +191,30 @@ cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev
   return cudaSuccess;
 }
 
+// In-place unnormalised 3D complex FFT (sign S) of buf on the plan's grid.
+template <typename R>
+cudaError_t launch_cfft3(atkm_plan* p, cx<R>* buf, int sign, cudaStream_t st) {
+  const Geo& g = p->g;
+  const Cst<R> c = make_cst<R>(g);
+  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const long nl = (long)g.Nz * g.Ny;
+  const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
+  const PassGrid gy = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
+  const PassGrid gz = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
+  const double fx = (double)nl * fftflops(g.Nx), fy = (double)g.Nz * g.Nx * fftflops(g.Ny),
+               fz = (double)g.Ny * g.Nx * fftflops(g.Nz);
+  if (sign < 0) {
+    { OpCX<R, -1> op; op.buf = buf; op.c = c; ATKM_RUN("fft3_x", 2 * N * s, fx, op, p->fN[0], gx); }
+    { OpPY<R, -1> op; op.Wk = buf; op.c = c; ATKM_RUN("fft3_y", 2 * N * s, fy, op, p->fN[1], gy); }
+    { OpCZ<R, -1> op; op.buf = buf; op.c = c; ATKM_RUN("fft3_z", 2 * N * s, fz, op, p->fN[2], gz); }
+  } else {
+    { OpCX<R, 1> op; op.buf = buf; op.c = c; ATKM_RUN("fft3_x", 2 * N * s, fx, op, p->fN[0], gx); }
+    { OpPY<R, 1> op; op.Wk = buf; op.c = c; ATKM_RUN("fft3_y", 2 * N * s, fy, op, p->fN[1], gy); }
+    { OpCZ<R, 1> op; op.buf = buf; op.c = c; ATKM_RUN("fft3_z", 2 * N * s, fz, op, p->fN[2], gz); }
+  }
+  return cudaSuccess;
+}
+
 #undef ATKM_RUN
 
 }  // namespace atkm

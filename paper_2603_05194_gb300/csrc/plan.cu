@@ -201,6 +201,24 @@ __global__ void k_to_f32(float* __restrict__ dst, const double* __restrict__ src
     dst[i] = (float)src[i];
 }
 
+// Fine spectrum <- coarse spectrum / Nc: fine frequency k (signed) takes the
+// coarse coefficient of the same k when -Nc/2 <= k < Nc/2, zero otherwise.
+__global__ void k_embed_spectrum(const double2* __restrict__ coarse, double2* __restrict__ fine, Geo gc, Geo gf,
+                                 double scale) {
+  const size_t total = (size_t)gf.Nx * gf.Ny * gf.Nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % gf.Nx), y = (int)((i / gf.Nx) % gf.Ny), z = (int)(i / ((size_t)gf.Nx * gf.Ny));
+    const int kx = x < gf.Nx / 2 ? x : x - gf.Nx, ky = y < gf.Ny / 2 ? y : y - gf.Ny, kz = z < gf.Nz / 2 ? z : z - gf.Nz;
+    double2 v = make_double2(0.0, 0.0);
+    if (kx >= -gc.Nx / 2 && kx < gc.Nx / 2 && ky >= -gc.Ny / 2 && ky < gc.Ny / 2 && kz >= -gc.Nz / 2 && kz < gc.Nz / 2) {
+      const int cx = (kx + gc.Nx) % gc.Nx, cy = (ky + gc.Ny) % gc.Ny, cz = (kz + gc.Nz) % gc.Nz;
+      const double2 c = coarse[((size_t)cz * gc.Ny + cy) * gc.Nx + cx];
+      v = make_double2(scale * c.x, scale * c.y);
+    }
+    fine[i] = v;
+  }
+}
+
 bool smooth235(int n) {
   if (n <= 0) return false;
   for (int r : {2, 3, 5})
@@ -611,6 +629,29 @@ int atkm_plan_kernel_stats(atkm_plan* plan, atkm_kernel_stat* out, int capacity,
   *count = (int)agg.size();
   for (int i = 0; i < capacity && i < (int)agg.size(); ++i) out[i] = agg[i];
   return ATKM_OK;
+}
+
+int atkm_spectral_upsample(atkm_plan* coarse, atkm_plan* fine, const double* psi_c, double* psi_f, void* stream) {
+  if (!coarse || !fine || !psi_c || !psi_f) return fail(nullptr, ATKM_ERR_ARG, "atkm_spectral_upsample: NULL argument");
+  const Geo &gc = coarse->g, &gf = fine->g;
+  const double Lc[3] = {gc.Lx, gc.Ly, gc.Lz}, Lf[3] = {gf.Lx, gf.Ly, gf.Lz};
+  const int Nc[3] = {gc.Nx, gc.Ny, gc.Nz}, Nf[3] = {gf.Nx, gf.Ny, gf.Nz};
+  for (int a = 0; a < 3; ++a) {
+    if (fabs(Lc[a] - Lf[a]) > 1e-12 * Lc[a])
+      return fail(fine, ATKM_ERR_ARG, "atkm_spectral_upsample: coarse and fine plans must share the box");
+    if (Nf[a] < Nc[a]) return fail(fine, ATKM_ERR_ARG, "atkm_spectral_upsample: fine grid must not be coarser");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = (size_t)gc.Nx * gc.Ny * gc.Nz;
+  cudaError_t e = cudaMemcpyAsync(coarse->T1, psi_c, nc * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = launch_cfft3<double>(coarse, coarse->T1, -1, st);
+  if (e == cudaSuccess) {
+    k_embed_spectrum<<<1216, 256, 0, st>>>(coarse->T1, reinterpret_cast<double2*>(psi_f), gc, gf, 1.0 / (double)nc);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_cfft3<double>(fine, reinterpret_cast<double2*>(psi_f), 1, st);
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(fine, e, "atkm_spectral_upsample");
 }
 
 }  // extern "C"
