@@ -204,6 +204,7 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=40)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save-params", default=None, help="write the trained parameters (.npy)")
     a = ap.parse_args(argv)
     B.load_library()
     psi0 = lambda p: W.initial_guess(p)  # noqa: E731  guess (d) on the problem's grid
@@ -227,6 +228,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     loss_tr, loss_ho = loss_of(net, f_tr, t_tr), loss_of(net, f_ho, t_ho)
+    if a.save_params:
+        np.save(a.save_params, net.get_params().cpu().numpy())
     print(f"train loss {loss_tr:.4e}, held-out loss {loss_ho:.4e}")
     eval_p = [W.with_grid(p, W.GUESS_FINE_N) for p in W.guess_draws(a.eval, seed=6)]
     ev = evaluate(net, eval_p, psi0, W.GUESS_FINE_N, 1e-8, a.eval_iters, chunk=a.chunk)
