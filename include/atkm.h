@@ -188,7 +188,9 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
 
 /* Precision modes of the PCG driver. */
 #define ATKM_PRECISION_F64 0      /* every step in FP64                          */
-#define ATKM_PRECISION_F32_F64 1  /* complex64 FFT/ATKM/H/P until switch_tol, then FP64 */
+#define ATKM_PRECISION_F32_F64 1  /* complex64 FFT/ATKM/H/P until switch_tol, two exhausted
+                                     halving loops, or 400 iterations without halving the
+                                     best FP32 residual; then FP64                     */
 
 typedef struct atkm_pcg_opts {
   double tol_residual;  /* stop when ||H phi - mu phi|| <= tol_residual (e.g. 1e-8)    */
@@ -242,11 +244,12 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
  * pcg_ground_state_batched -- `count` independent solves of Algorithm 1 (an
  * Omega or anisotropy sweep) on one GPU.  Grids may differ: instance i uses
  * plans[i] (each instance needs its own plan), prm[i], psi[i] (device, in/out)
- * and out[i] (its log pointer is honoured); all share `opts`.  Each batched
- * round replays every active instance's captured iteration graph on that
- * instance's plan stream, so instances run concurrently on the GPU, then
- * reads all control blocks with one synchronisation per stream.  Results are
- * bitwise identical to pcg_ground_state on each instance alone.  Returns
+ * and out[i] (its log pointer is honoured); all share `opts`.  Every instance
+ * replays its captured iteration graph on its own plan stream, so instances
+ * run concurrently on the GPU; the host polls the streams and processes and
+ * relaunches each instance as soon as its last phase has finished (small
+ * grids do not wait for large ones).  Results are bitwise identical to
+ * pcg_ground_state on each instance alone.  Returns
  * ATKM_OK if every instance converged, else the first non-OK status
  * (ATKM_ERR_CUDA takes precedence); per-instance statuses are in out[i].status.
  */
@@ -265,6 +268,24 @@ int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_para
  */
 int atkm_spectral_upsample(atkm_plan* coarse, atkm_plan* fine, const double* psi_c, double* psi_f,
                            void* stream);
+
+/*
+ * pcg_ground_state_mg -- the cascadic multigrid driver PCG-ATKM-MG
+ * (Algorithm 2): for level i = 0 .. levels-1 (coarse to fine), compute the
+ * ground state on plans[i] by Algorithm 1 (pcg_ground_state with `opts`)
+ * starting from psi[i], then (Step 2) set psi[i+1] to its Fourier interpolant
+ * on the next grid (atkm_spectral_upsample).  The plans share the box and the
+ * dipole axis; grids must not get coarser.  The paper's setting is three
+ * levels with N_a/4, N_a/2, N_a points per axis.
+ *   psi     `levels` device buffers, psi[i] of plans[i]'s size; psi[0] holds
+ *           the initial guess; every psi[i] ends as level i's ground state.
+ *   out     `levels` host result structs (log pointers honoured).
+ * Returns the finest level's status (ATKM_OK when it converged); a level
+ * ending in NOT_CONVERGED or STAGNATED still seeds the next one; an error
+ * stops the cascade.  out[i].status holds each level's status.
+ */
+int pcg_ground_state_mg(int levels, atkm_plan* const* plans, const atkm_params* prm,
+                        const atkm_pcg_opts* opts, double* const* psi, atkm_result* out, void* stream);
 
 /*
  * Learned initial guess.  The paper chooses psi_0 among fixed formulas (§3,

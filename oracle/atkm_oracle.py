@@ -436,3 +436,37 @@ def pcg_ground_state(plan: Plan, prm: Params, phi0, opts: PcgOptions = PcgOption
     parts = energy_parts(plan, prm, phi, Phi)
     return PcgResult(phi=phi, Phi=Phi, status=status, iters=n, residual=res, mu=mu,
                      parts=parts, halvings=total_halvings, linf_step=linf, log=log)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2: cascadic multigrid (PCG-ATKM-MG)
+# ---------------------------------------------------------------------------
+
+def spectral_upsample(psi_c, Nf) -> np.ndarray:
+    """Fourier interpolant (Eq. (Fourphi)) of a coarse grid function evaluated
+    on a finer grid of the same box: the coefficients of k in Lambda_Nc are
+    kept, every other coefficient of the fine grid is zero."""
+    Nz, Ny, Nx = psi_c.shape
+    c = np.fft.fftn(psi_c) / psi_c.size
+    fine = np.zeros((Nf[2], Nf[1], Nf[0]), dtype=np.complex128)
+    for kz in range(-Nz // 2, Nz // 2):
+        for ky in range(-Ny // 2, Ny // 2):
+            fine[kz % Nf[2], ky % Nf[1], np.arange(-Nx // 2, Nx // 2) % Nf[0]] = \
+                c[kz % Nz, ky % Ny, np.arange(-Nx // 2, Nx // 2) % Nx]
+    return np.fft.ifftn(fine) * fine.size
+
+
+def pcg_ground_state_mg(plans, prm: Params, phi0, opts: PcgOptions = PcgOptions()) -> list:
+    """Algorithm 2: on each mesh from the coarsest to the finest, Step 1 runs
+    Algorithm 1 from the current initial data, Step 2 interpolates its ground
+    state onto the next mesh (the Fourier interpolant above).  Returns the
+    PcgResult of every level."""
+    out = []
+    phi = phi0
+    for i, plan in enumerate(plans):
+        res = pcg_ground_state(plan, prm, phi, opts)
+        out.append(res)
+        if i + 1 < len(plans):
+            phi = spectral_upsample(res.phi, plans[i + 1].grid.N)
+    return out
+

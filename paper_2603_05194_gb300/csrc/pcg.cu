@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <initializer_list>
 #include <utility>
+#include <thread>
 #include <vector>
 
 #include "atkm_internal.cuh"
@@ -671,6 +672,10 @@ static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
 // block on the plan stream; wait() synchronises that stream; process() takes
 // the decisions of the stop rule, the halving loop and the log.  Several
 // solvers on different plans run concurrently (pcg_ground_state_batched).
+// FP32 phase stagnation: no halving of the best FP32 residual for this many
+// iterations hands over to FP64 (slow but steady phases halve it well within).
+constexpr int kF32Window = 400;
+
 struct Solver {
   enum State { INIT_CHECK, MAIN, HALVE, FORCED, FINAL, DONE };
   atkm_plan* plan = nullptr;
@@ -829,7 +834,7 @@ struct Solver {
         }
         if (h.nan) { status = ATKM_ERR_NAN; st = DONE; return; }
         if (f32 && h.res < 0.5 * f32_best) { f32_best = h.res; f32_best_n = n; }
-        if (f32 && (h.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > 100)) {
+        if (f32 && (h.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > kF32Window)) {
           // hand over to FP64: recompute Phi in FP64, re-evaluate this phi, restart the direction
           f32 = false;
           caps = 0;
@@ -1003,17 +1008,25 @@ int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_para
     for (int i = 0; i < count; ++i) S[i].abandon();
     return first_err;
   }
-  // One batched round: every active instance enqueues its next phase on its
-  // own stream (they overlap on the GPU), then all are awaited and processed.
+  // Event-driven rounds: every instance enqueues its next phase on its own
+  // stream as soon as its previous phase has finished and been processed, so
+  // small grids keep iterating while large ones are still on the GPU.
+  for (auto& s : S)
+    if (!s.done()) s.launch();
   while (true) {
-    bool any = false;
-    for (auto& s : S)
-      if (!s.done()) { s.launch(); any = true; }
+    bool any = false, progressed = false;
+    for (auto& s : S) {
+      if (s.done()) continue;
+      any = true;
+      const cudaError_t q = cudaStreamQuery(s.B->st);
+      if (q == cudaErrorNotReady) continue;
+      s.wait();  // returns at once (or records the stream's error)
+      s.process();
+      if (!s.done()) s.launch();
+      progressed = true;
+    }
     if (!any) break;
-    for (auto& s : S)
-      if (!s.done()) s.wait();
-    for (auto& s : S)
-      if (!s.done()) s.process();
+    if (!progressed) std::this_thread::yield();
   }
   int worst = ATKM_OK;
   for (auto& s : S) {
@@ -1022,6 +1035,33 @@ int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_para
     if (code == ATKM_ERR_CUDA) worst = code;
   }
   return worst;
+}
+
+int pcg_ground_state_mg(int levels, atkm_plan* const* plans, const atkm_params* prm, const atkm_pcg_opts* opts,
+                        double* const* psi, atkm_result* out, void* stream) {
+  if (levels < 1 || !plans || !prm || !opts || !psi || !out)
+    return fail(nullptr, ATKM_ERR_ARG, "pcg_ground_state_mg: bad level count or NULL argument");
+  for (int i = 0; i < levels; ++i)
+    if (!plans[i] || !psi[i]) return fail(nullptr, ATKM_ERR_ARG, "pcg_ground_state_mg: NULL plan or buffer");
+  for (int i = 0; i + 1 < levels; ++i) {
+    const Geo &a = plans[i]->g, &b = plans[i + 1]->g;
+    if (plans[i] == plans[i + 1] || psi[i] == psi[i + 1])
+      return fail(nullptr, ATKM_ERR_ARG, "pcg_ground_state_mg: levels need distinct plans and buffers");
+    if (b.Nx < a.Nx || b.Ny < a.Ny || b.Nz < a.Nz)
+      return fail(nullptr, ATKM_ERR_ARG, "pcg_ground_state_mg: grids must not get coarser");
+  }
+  atkm_pcg_opts o = *opts;
+  o.resume = 0;
+  int code = ATKM_OK;
+  for (int i = 0; i < levels; ++i) {
+    code = pcg_ground_state(plans[i], prm, &o, psi[i], &out[i], stream);
+    if (code != ATKM_OK && code != ATKM_NOT_CONVERGED && code != ATKM_STAGNATED) return code;
+    if (i + 1 < levels) {
+      const int up = atkm_spectral_upsample(plans[i], plans[i + 1], psi[i], psi[i + 1], stream);
+      if (up != ATKM_OK) return up;
+    }
+  }
+  return code;
 }
 
 }  // extern "C"
