@@ -176,6 +176,13 @@ def measured_peaks() -> dict:
 FP64_PEAK_GFLOPS = 1255.0
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# passes that can be the dominant kernel, from one ncu capture of the current
+# kernels on this workload (the profile file gives the command).  A kernel not
+# listed here reports traffic null.
+NCU_TRAFFIC = {}
+
+
 # ------------------------------------------------------------------ ours
 def atkm_evals(stats) -> int:
     """ATKM evaluations in a profiling record: one x-forward pass each."""
@@ -204,13 +211,17 @@ def roofline(stats, peaks):
         achieved = dom["bytes_total"] / (dom["ms_total"] * 1e-3) / 1e9
         return {"kernel": dom["name"], "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": NCU_TRAFFIC.get(dom["name"], {}).get("bytes"),
+                "traffic_source": NCU_TRAFFIC.get(dom["name"], {}).get("profile"),
                 "algorithmic_bytes_per_launch": dom["bytes_total"] / dom["launches"],
                 "launch_ms": round(per_launch_ms, 4), "launches": dom["launches"]}
     achieved = dom["flops_total"] / (dom["ms_total"] * 1e-3) / 1e9
     return {"kernel": dom["name"], "bound": "alu", "achieved": round(achieved, 1), "peak": FP64_PEAK_GFLOPS,
             "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-            "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300", "traffic": None,
+            "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300",
+            "traffic": NCU_TRAFFIC.get(dom["name"], {}).get("bytes"),
+            "traffic_source": NCU_TRAFFIC.get(dom["name"], {}).get("profile"),
             "algorithmic_flops_per_launch": dom["flops_total"] / dom["launches"],
             "algorithmic_bytes_per_launch": dom["bytes_total"] / dom["launches"],
             "hbm_GBs": round(dom["bytes_total"] / (dom["ms_total"] * 1e-3) / 1e9, 1),
@@ -372,7 +383,7 @@ def main():
     if rank == 0:
         res = out["res"]
         value = out["evals"] / (out["ms"] * 1e-3)
-        kernels = sorted(out["stats"], key=lambda k: -k["ms_total"])[:10]
+        kernels = sorted(out["stats"], key=lambda k: -k["ms_total"])[:24]
         ktable = [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms_total"], 3),
                    "GB/s": round(k["bytes_total"] / (k["ms_total"] * 1e-3) / 1e9, 1) if k["ms_total"] else None,
                    "GFLOP/s": round(k["flops_total"] / (k["ms_total"] * 1e-3) / 1e9, 1) if k["ms_total"] else None}
