@@ -22,6 +22,46 @@ template <typename R> using cx = typename CT<R>::c;
 template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
   cx<R> z; z.x = a; z.y = b; return z;
 }
+// binary64 <-> binary32 conversions for the FP32 passes done on the integer
+// pipe from the IEEE-754 bit layouts (the hardware conversion instructions
+// share the slow FP64 pipe on this part).  binary64 -> binary32 rounds the 29
+// dropped mantissa bits half-up (a mantissa carry moves into the exponent),
+// flushes results below the binary32 normal range to signed zero and
+// saturates to infinity; binary32 -> binary64 is exact for normal numbers and
+// flushes binary32 subnormals to signed zero.
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned int hi = (unsigned int)(u >> 32);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e >= 255) {
+    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (u & 0x000fffffffffffffull) != 0ull;
+    return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
+  }
+  if (e <= 0) return __uint_as_float(sign);
+  const unsigned long long m = u & 0x000fffffffffffffull;
+  unsigned int bits = ((unsigned int)e << 23) + (unsigned int)((m + (1ull << 28)) >> 29);
+  if (bits >= 0x7f800000u) bits = 0x7f800000u;
+  return __uint_as_float(sign | bits);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned int m = u & 0x7fffffu;
+  unsigned int hi, lo;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  else if (e == 255u) { hi = sign | 0x7ff00000u | (m >> 3); lo = (m & 7u) << 29; }
+  else { hi = sign | ((e + 896u) << 20) | (m >> 3); lo = (m & 7u) << 29; }
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+template <typename R> __device__ __forceinline__ R tor(double v);
+template <> __device__ __forceinline__ double tor<double>(double v) { return v; }
+template <> __device__ __forceinline__ float tor<float>(double v) { return d2f_bits(v); }
+template <typename R> __device__ __forceinline__ double tod(R v);
+template <> __device__ __forceinline__ double tod<double>(double v) { return v; }
+template <> __device__ __forceinline__ double tod<float>(float v) { return f2d_bits(v); }
+
 template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
 template <typename R> __device__ __forceinline__ cx<R> sub(cx<R> a, cx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
 template <typename R> __device__ __forceinline__ cx<R> scl(cx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
@@ -218,6 +258,31 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NS], double* pa
     double v = acc[s];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) red[s][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double v = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) v += red[s][w];
+      part[s * stride + slot] = v;
+    }
+  }
+}
+
+// The same for FP32 per-thread partials: the warp stage shuffles and adds in
+// FP32 (a 32-term sum, about 5 roundings), each warp's sum is widened once,
+// and the block stage adds in FP64 -- so no per-thread FP64 work is done in
+// FP32 kernels (the FP64 pipe is slow on this part).
+template <int NS>
+__device__ __forceinline__ void block_reduce_store_f32(float (&acc)[NS], double* part, int stride, int slot) {
+  __shared__ double red[NS][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    float v = acc[s];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[s][warp] = tod<float>(v);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -50,45 +50,6 @@ template <typename R> inline PhysR<R> make_physr(const Phys& p) {
 __device__ __forceinline__ int kfreq(int m, int M) { return m < (M >> 1) ? m : m - M; }
 __device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
 
-// binary64 <-> binary32 conversions for the FP32 passes done on the integer
-// pipe from the IEEE-754 bit layouts (the hardware conversion instructions
-// share the slow FP64 pipe on this part).  binary64 -> binary32 rounds the 29
-// dropped mantissa bits half-up (a mantissa carry moves into the exponent),
-// flushes results below the binary32 normal range to signed zero and
-// saturates to infinity; binary32 -> binary64 is exact for normal numbers and
-// flushes binary32 subnormals to signed zero.
-__device__ __forceinline__ float d2f_bits(double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  const unsigned int hi = (unsigned int)(u >> 32);
-  const unsigned int sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e >= 255) {
-    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (u & 0x000fffffffffffffull) != 0ull;
-    return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
-  }
-  if (e <= 0) return __uint_as_float(sign);
-  const unsigned long long m = u & 0x000fffffffffffffull;
-  unsigned int bits = ((unsigned int)e << 23) + (unsigned int)((m + (1ull << 28)) >> 29);
-  if (bits >= 0x7f800000u) bits = 0x7f800000u;
-  return __uint_as_float(sign | bits);
-}
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int sign = u & 0x80000000u;
-  const unsigned int e = (u >> 23) & 0xffu;
-  const unsigned int m = u & 0x7fffffu;
-  unsigned int hi, lo;
-  if (e == 0u) { hi = sign; lo = 0u; }
-  else if (e == 255u) { hi = sign | 0x7ff00000u | (m >> 3); lo = (m & 7u) << 29; }
-  else { hi = sign | ((e + 896u) << 20) | (m >> 3); lo = (m & 7u) << 29; }
-  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-}
-template <typename R> __device__ __forceinline__ R tor(double v);
-template <> __device__ __forceinline__ double tor<double>(double v) { return v; }
-template <> __device__ __forceinline__ float tor<float>(double v) { return d2f_bits(v); }
-template <typename R> __device__ __forceinline__ double tod(R v);
-template <> __device__ __forceinline__ double tod<double>(double v) { return v; }
-template <> __device__ __forceinline__ double tod<float>(float v) { return f2d_bits(v); }
 template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { return mk<R>(tor<R>(z.x), tor<R>(z.y)); }
 template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R)0, (R)0); }
 
@@ -184,14 +145,15 @@ template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
 // ------------------------------------------------------------ kernels
 template <typename R, int NR>
 __device__ __forceinline__ void reduce_out(R (&acc)[NR], double* part, int pstride) {
-  double d[NR];
-#pragma unroll
-  for (int s = 0; s < NR; ++s) d[s] = (double)acc[s];
-  block_reduce_store<NR>(d, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
+  if constexpr (sizeof(R) == 4) {
+    block_reduce_store_f32<NR>(acc, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
+  } else {
+    block_reduce_store<NR>(acc, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
+  }
 }
 
 template <typename R, int L, class Op>
-__global__ void __launch_bounds__(kThreads) k_fast(Op op, const cx<R>* __restrict__ twg) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1) k_fast(Op op, const cx<R>* __restrict__ twg) {
   using C = FastCfg<L>;
   extern __shared__ __align__(16) unsigned char fast_smem[];
   cx<R>* tw = reinterpret_cast<cx<R>*>(fast_smem);

@@ -23,7 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
-#include <initializer_list>
+#include <mutex>
 #include <utility>
 #include <thread>
 #include <vector>
@@ -73,6 +73,8 @@ __global__ void k_finalize(const double* __restrict__ part, int nblocks, double*
   if (threadIdx.x == 0) out[s] = sh[0];
 }
 
+// Grid maximum of the block maxima; out = its square root (the partials hold
+// squared distances).
 __global__ void k_finalize_max(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
   __shared__ double sh[kRedThreads];
   double acc = 0.0;
@@ -83,53 +85,95 @@ __global__ void k_finalize_max(const double* __restrict__ part, int nblocks, dou
     if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sh[0];
+  if (threadIdx.x == 0) out[0] = sqrt(sh[0]);
 }
 
-constexpr int kMaxDots = 8;
-struct DotPairs {
-  const double2* u[kMaxDots];
-  const double2* v[kMaxDots];
-  int n;
-};
+// Vector kernels of the driver.  Vectors are FP64 in memory.  T is the type
+// of the per-element arithmetic: double in the FP64 phase; float in the FP32
+// phase of the precision form, where every operand carries FP32-level
+// accuracy only (H, ATKM and P ran in FP32) and FP64 products would only burn
+// the slow FP64 pipe.  With T = float, loads convert on the integer pipe,
+// sums accumulate per thread in FP32 over chunks of kChunk elements and in
+// FP64 beyond (block and grid sums are FP64 in both phases).
+constexpr int kChunk = 8;
 
-// sum_j Re(u_j conj(v_j)) for up to 8 pairs in one sweep.
-__global__ void __launch_bounds__(kRedThreads) k_dots(DotPairs dp, size_t N, double* __restrict__ part) {
-  double acc[kMaxDots];
+template <typename T> struct V2 { T x, y; };
+template <typename T> __device__ __forceinline__ V2<T> ld2(const double2& a) { return V2<T>{tor<T>(a.x), tor<T>(a.y)}; }
+template <typename T> __device__ __forceinline__ T ld1(double a) { return tor<T>(a); }
+template <typename T> __device__ __forceinline__ T dotr(V2<T> a, V2<T> b) { return a.x * b.x + a.y * b.y; }
+
+template <typename T, int NS> struct Sums {
+  double d[NS];
+  T f[NS];
+  int n;
+  __device__ __forceinline__ Sums() : n(0) {
 #pragma unroll
-  for (int i = 0; i < kMaxDots; ++i) acc[i] = 0.0;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
+    for (int s = 0; s < NS; ++s) { d[s] = 0.0; f[s] = (T)0; }
+  }
+  __device__ __forceinline__ void add(int s, T v) {
+    if constexpr (sizeof(T) == 8) d[s] += v;
+    else f[s] += v;
+  }
+  __device__ __forceinline__ void flush() {
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int i = 0; i < kMaxDots; ++i) {
-      if (i < dp.n) {
-        const double2 a = dp.u[i][j], b = dp.v[i][j];
-        acc[i] += a.x * b.x + a.y * b.y;
-      }
+      for (int s = 0; s < NS; ++s) { d[s] += tod<T>(f[s]); f[s] = (T)0; }
+    }
+    n = 0;
+  }
+  __device__ __forceinline__ void next() {
+    if constexpr (sizeof(T) == 4) {
+      if (++n == kChunk) flush();
     }
   }
-  block_reduce_store<kMaxDots>(acc, part, gridDim.x, blockIdx.x);
+  // Block sums into part[s * gridDim.x + blockIdx.x].  FP32 kernels hand each
+  // thread's total to the FP32 warp stage (no per-thread FP64 shuffles).
+  __device__ __forceinline__ void store(double* part) {
+    flush();
+    if constexpr (sizeof(T) == 4) {
+      float v[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) v[s] = tor<float>(d[s]);
+      block_reduce_store_f32<NS>(v, part, gridDim.x, blockIdx.x);
+    } else {
+      block_reduce_store<NS>(d, part, gridDim.x, blockIdx.x);
+    }
+  }
+};
+
+#define ATKM_GRID_LOOP(j, N) \
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < (N); j += (size_t)gridDim.x * blockDim.x)
+
+// sum_j Re(u_j conj(v_j)) (FP64).
+__global__ void __launch_bounds__(kRedThreads) k_dot(const double2* __restrict__ u, const double2* __restrict__ v,
+                                                     size_t N, double* __restrict__ part) {
+  Sums<double, 1> acc;
+  ATKM_GRID_LOOP(j, N) {
+    const double2 a = u[j], b = v[j];
+    acc.add(0, a.x * b.x + a.y * b.y);
+  }
+  acc.store(part);
 }
 
 // The seven sums of the direction step from one read of its five vectors:
-// <Pr,phi>, <r,Pr>, <r,phi>, <r_prev,Pr>, <r_prev,phi>, <p_prev,phi>, <phi,phi>
-// (same per-element order as k_dots on the seven pairs).
+// <Pr,phi>, <r,Pr>, <r,phi>, <r_prev,Pr>, <r_prev,phi>, <p_prev,phi>, <phi,phi>.
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_dir_dots(const double2* __restrict__ Pr, const double2* __restrict__ phi, const double2* __restrict__ r,
            const double2* __restrict__ rp, const double2* __restrict__ pp, size_t N, double* __restrict__ part) {
-  double acc[kMaxDots];
-#pragma unroll
-  for (int i = 0; i < kMaxDots; ++i) acc[i] = 0.0;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
-    const double2 P = Pr[j], f = phi[j], a = r[j], b = rp[j], c = pp[j];
-    acc[0] += P.x * f.x + P.y * f.y;
-    acc[1] += a.x * P.x + a.y * P.y;
-    acc[2] += a.x * f.x + a.y * f.y;
-    acc[3] += b.x * P.x + b.y * P.y;
-    acc[4] += b.x * f.x + b.y * f.y;
-    acc[5] += c.x * f.x + c.y * f.y;
-    acc[6] += f.x * f.x + f.y * f.y;
+  Sums<T, 7> acc;
+  ATKM_GRID_LOOP(j, N) {
+    const V2<T> P = ld2<T>(Pr[j]), f = ld2<T>(phi[j]), a = ld2<T>(r[j]), b = ld2<T>(rp[j]), c = ld2<T>(pp[j]);
+    acc.add(0, dotr(P, f));
+    acc.add(1, dotr(a, P));
+    acc.add(2, dotr(a, f));
+    acc.add(3, dotr(b, P));
+    acc.add(4, dotr(b, f));
+    acc.add(5, dotr(c, f));
+    acc.add(6, dotr(f, f));
+    acc.next();
   }
-  block_reduce_store<kMaxDots>(acc, part, gridDim.x, blockIdx.x);
+  acc.store(part);
 }
 
 // A coefficient m * (*p) (p may be null: then m).
@@ -141,38 +185,43 @@ __device__ __forceinline__ double cval(const Coef& c) { return c.p ? c.m * *c.p 
 
 // out = c0 v0 + c1 v1 + c2 v2 (null vectors skipped); sums |out|^2 and
 // Re(w conj(out)) when w is given.  Skipped entirely when *pred == 0.
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_lincomb(double2* __restrict__ out, const double2* __restrict__ v0, Coef c0, const double2* __restrict__ v1,
           Coef c1, const double2* __restrict__ v2, Coef c2, const double2* __restrict__ w, size_t N,
           double* __restrict__ part, const int* __restrict__ pred) {
   if (pred && !*pred) return;
-  const double a0 = cval(c0), a1 = cval(c1), a2 = cval(c2);
-  double acc[2] = {0.0, 0.0};
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
-    double2 o = make_double2(0.0, 0.0);
-    if (v0) { const double2 a = v0[j]; o.x += a0 * a.x; o.y += a0 * a.y; }
-    if (v1) { const double2 a = v1[j]; o.x += a1 * a.x; o.y += a1 * a.y; }
-    if (v2) { const double2 a = v2[j]; o.x += a2 * a.x; o.y += a2 * a.y; }
-    out[j] = o;
-    acc[0] += o.x * o.x + o.y * o.y;
-    if (w) { const double2 b = w[j]; acc[1] += b.x * o.x + b.y * o.y; }
+  const T a0 = tor<T>(cval(c0)), a1 = tor<T>(cval(c1)), a2 = tor<T>(cval(c2));
+  Sums<T, 2> acc;
+  ATKM_GRID_LOOP(j, N) {
+    V2<T> o{(T)0, (T)0};
+    if (v0) { const V2<T> a = ld2<T>(v0[j]); o.x += a0 * a.x; o.y += a0 * a.y; }
+    if (v1) { const V2<T> a = ld2<T>(v1[j]); o.x += a1 * a.x; o.y += a1 * a.y; }
+    if (v2) { const V2<T> a = ld2<T>(v2[j]); o.x += a2 * a.x; o.y += a2 * a.y; }
+    out[j] = make_double2(tod<T>(o.x), tod<T>(o.y));
+    acc.add(0, dotr(o, o));
+    if (w) acc.add(1, dotr(ld2<T>(w[j]), o));
+    acc.next();
   }
-  block_reduce_store<2>(acc, part, gridDim.x, blockIdx.x);
+  acc.store(part);
 }
 
-// phi+ *= *inv; block max of |phi+ - phi|.
+// phi+ *= *inv (FP64: the renormalisation); block max of |phi+ - phi|^2, the
+// difference taken in T (FP32 in the FP32 phase, where it is only logged).
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_scale_linf(double2* __restrict__ phin, const double2* __restrict__ phi, const double* __restrict__ invp, size_t N,
              double* __restrict__ part) {
-  __shared__ double sh[kRedThreads];
+  __shared__ T sh[kRedThreads];
   const double inv = *invp;
-  double m = 0.0;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
+  T m = (T)0;
+  ATKM_GRID_LOOP(j, N) {
     double2 a = phin[j];
     a.x *= inv; a.y *= inv;
     phin[j] = a;
-    const double2 b = phi[j];
-    m = fmax(m, hypot(a.x - b.x, a.y - b.y));
+    const V2<T> x = ld2<T>(a), y = ld2<T>(phi[j]);
+    const T dx = x.x - y.x, dy = x.y - y.y;
+    m = fmax(m, dx * dx + dy * dy);
   }
   sh[threadIdx.x] = m;
   __syncthreads();
@@ -180,39 +229,47 @@ k_scale_linf(double2* __restrict__ phin, const double2* __restrict__ phi, const 
     if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = tod<T>(sh[0]);
 }
 
-// Sums for the curvature and the trial energy:
-//   [0] sum rho'(beta rho' + lambda Phi'),  rho' = Re(conj(phi) p)
-//   [1] sum (beta|phi|^2 + lambda Phi) Re(phi conj(p))
-//   [2] sum (beta|phi|^2 + lambda Phi) |p|^2
+// Sums for the curvature of the quadratic model:
+//   [0] <Hp, p>
+//   [1] sum rho'(beta rho' + lambda Phi'),  rho' = Re(conj(phi) p)
+//   [2] sum (beta|phi|^2 + lambda Phi) Re(phi conj(p))
+//   [3] sum (beta|phi|^2 + lambda Phi) |p|^2
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-k_curv_sums(const double2* __restrict__ phi, const double2* __restrict__ p, const double* __restrict__ Phi,
-            const double* __restrict__ Phi1, double beta, double lambda, size_t N, double* __restrict__ part) {
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = phi[j], b = p[j];
-    const double rp = a.x * b.x + a.y * b.y;
-    const double w = beta * (a.x * a.x + a.y * a.y) + lambda * Phi[j];
-    acc[0] += rp * (beta * rp + lambda * Phi1[j]);
-    acc[1] += w * rp;
-    acc[2] += w * (b.x * b.x + b.y * b.y);
+k_curv_sums(const double2* __restrict__ Hp, const double2* __restrict__ phi, const double2* __restrict__ p,
+            const double* __restrict__ Phi, const double* __restrict__ Phi1, double beta, double lambda, size_t N,
+            double* __restrict__ part) {
+  const T bt = tor<T>(beta), lm = tor<T>(lambda);
+  Sums<T, 4> acc;
+  ATKM_GRID_LOOP(j, N) {
+    const V2<T> a = ld2<T>(phi[j]), b = ld2<T>(p[j]), h = ld2<T>(Hp[j]);
+    const T rp = dotr(a, b);
+    const T w = bt * dotr(a, a) + lm * ld1<T>(Phi[j]);
+    acc.add(0, dotr(h, b));
+    acc.add(1, rp * (bt * rp + lm * ld1<T>(Phi1[j])));
+    acc.add(2, w * rp);
+    acc.add(3, w * dotr(b, b));
+    acc.next();
   }
-  block_reduce_store<3>(acc, part, gridDim.x, blockIdx.x);
+  acc.store(part);
 }
 
 // [0] sum |phi|^4, [1] sum Phi |phi|^2
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_quartic_sums(const double2* __restrict__ phi, const double* __restrict__ Phi, size_t N, double* __restrict__ part) {
-  double acc[2] = {0.0, 0.0};
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N; j += (size_t)gridDim.x * blockDim.x) {
-    const double2 a = phi[j];
-    const double r = a.x * a.x + a.y * a.y;
-    acc[0] += r * r;
-    acc[1] += Phi[j] * r;
+  Sums<T, 2> acc;
+  ATKM_GRID_LOOP(j, N) {
+    const V2<T> a = ld2<T>(phi[j]);
+    const T r = dotr(a, a);
+    acc.add(0, r * r);
+    acc.add(1, ld1<T>(Phi[j]) * r);
+    acc.next();
   }
-  block_reduce_store<2>(acc, part, gridDim.x, blockIdx.x);
+  acc.store(part);
 }
 
 __global__ void k_set_scalar(double* dst, double v) { *dst = v; }
@@ -224,13 +281,48 @@ int red_grid(size_t N) {
   return (int)b;
 }
 
+// Grid of a grid-stride vector kernel: whole waves (SMs x resident blocks of
+// that kernel, from the occupancy calculator, cached per kernel), at most
+// red_grid(N) -- a partial last wave would leave SMs idle at the end.
+int wave_grid(const void* kernel, size_t N) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> cache;
+  static int nsm = 0;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (nsm == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        nsm = 152;
+      }
+    }
+    for (auto& kv : cache)
+      if (kv.first == kernel) per_sm = kv.second;
+    if (per_sm == 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRedThreads, 0) != cudaSuccess ||
+          per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 4;
+      }
+      cache.emplace_back(kernel, per_sm);
+    }
+  }
+  const size_t full = (size_t)nsm * per_sm;
+  const size_t cap = (size_t)red_grid(N);
+  if (cap < full) return (int)cap;
+  return (int)(full > (size_t)kRedGrid ? (kRedGrid / nsm) * nsm : full);
+}
+
 // Slots of plan->scal used by the driver.
 enum {
   S_H = SC_RED,          // 10 slots of the H phi reductions
   S_R = SC_RED + 10,     // |r|^2 (+ unused)
   S_D = SC_RED + 12,     // 7 dots for the direction
   S_P = SC_RED + 20,     // |p|^2, <H phi, p>
-  S_C = SC_RED + 22,     // <Hp,p>  then 3 curvature sums at S_C+1
+  S_C = SC_RED + 22,     // <Hp,p> and the 3 curvature sums
   S_T = SC_RED + 26,     // |phi+|^2 (+ unused)
   S_Q = SC_RED + 28,     // 2 quartic sums of phi+
   S_L = SC_RED + 30,     // linf
@@ -486,26 +578,29 @@ struct Seq {
   const double* s() const { return p->scal; }
   cudaStream_t st() const { return B.st; }
   void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
-  int G() const { return red_grid(B.N); }
 
-  void dots(std::initializer_list<std::pair<const double2*, const double2*>> pairs, int dst) {
-    DotPairs dp;
-    memset(&dp, 0, sizeof(dp));
-    for (auto& pr : pairs) { dp.u[dp.n] = pr.first; dp.v[dp.n] = pr.second; ++dp.n; }
-    prof_begin(p, "vec_dots", 32.0 * dp.n * B.N, 0.0, st());
-    k_dots<<<G(), kRedThreads, 0, st()>>>(dp, B.N, p->partials);
+  void dot(const double2* u, const double2* v, int dst) {
+    prof_begin(p, "vec_dots", 32.0 * B.N, 0.0, st());
+    const int g = wave_grid((const void*)k_dot, B.N);
+    k_dot<<<g, kRedThreads, 0, st()>>>(u, v, B.N, p->partials);
     prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
-    chk(launch_finalize(p, dp.n, G(), dst, st()));
+    chk(launch_finalize(p, 1, g, dst, st()));
   }
+  // FP64 arithmetic unless this is the FP32 phase and `phase_type` allows it.
   void lincomb(double2* out, const double2* v0, Coef c0, const double2* v1, Coef c1, const double2* v2, Coef c2,
-               const double2* w, int dst, const int* pred = nullptr) {
+               const double2* w, int dst, const int* pred = nullptr, bool phase_type = true) {
     const double nv = (v0 ? 1 : 0) + (v1 ? 1 : 0) + (v2 ? 1 : 0) + (w ? 1 : 0) + 1;
     prof_begin(p, "vec_lincomb", 16.0 * nv * B.N, 0.0, st());
-    k_lincomb<<<G(), kRedThreads, 0, st()>>>(out, v0, c0, v1, c1, v2, c2, w, B.N, p->partials, pred);
+    const bool fl = f32 && phase_type;
+    const int g = fl ? wave_grid((const void*)k_lincomb<float>, B.N) : wave_grid((const void*)k_lincomb<double>, B.N);
+    if (fl)
+      k_lincomb<float><<<g, kRedThreads, 0, st()>>>(out, v0, c0, v1, c1, v2, c2, w, B.N, p->partials, pred);
+    else
+      k_lincomb<double><<<g, kRedThreads, 0, st()>>>(out, v0, c0, v1, c1, v2, c2, w, B.N, p->partials, pred);
     prof_end(p, st());
-    k_finalize<<<2, kRedThreads, 0, st()>>>(p->partials, G(), p->scal + dst, pred);
+    k_finalize<<<2, kRedThreads, 0, st()>>>(p->partials, g, p->scal + dst, pred);
     count_launches(2);
     chk(cudaGetLastError());
   }
@@ -537,21 +632,27 @@ struct Seq {
   void trial() {
     double2* phin = B.phi[q ^ 1];
     lincomb(phin, B.phi[q], Coef{&c()->cr, 1.0}, B.p[q], Coef{&c()->sr, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr,
-            S_T);
+            S_T, nullptr, false);  // the retraction stays FP64
     ctl1(k_c_norm, c(), s());
     prof_begin(p, "vec_scale_linf", 48.0 * B.N, 0.0, st());
-    k_scale_linf<<<G(), kRedThreads, 0, st()>>>(phin, B.phi[q], &c()->inv, B.N, p->partials);
+    const int gs = f32 ? wave_grid((const void*)k_scale_linf<float>, B.N)
+                       : wave_grid((const void*)k_scale_linf<double>, B.N);
+    if (f32) k_scale_linf<float><<<gs, kRedThreads, 0, st()>>>(phin, B.phi[q], &c()->inv, B.N, p->partials);
+    else k_scale_linf<double><<<gs, kRedThreads, 0, st()>>>(phin, B.phi[q], &c()->inv, B.N, p->partials);
     prof_end(p, st());
-    k_finalize_max<<<1, kRedThreads, 0, st()>>>(p->partials, G(), p->scal + S_L);
+    k_finalize_max<<<1, kRedThreads, 0, st()>>>(p->partials, gs, p->scal + S_L);
     count_launches(2);
     chk(cudaGetLastError());
     atkm(SRC_PSI, reinterpret_cast<const double*>(phin), nullptr, B.Phi[q ^ 1]);
     prof_begin(p, "vec_quartic", 24.0 * B.N, 0.0, st());
-    k_quartic_sums<<<G(), kRedThreads, 0, st()>>>(phin, B.Phi[q ^ 1], B.N, p->partials);
+    const int gq = f32 ? wave_grid((const void*)k_quartic_sums<float>, B.N)
+                       : wave_grid((const void*)k_quartic_sums<double>, B.N);
+    if (f32) k_quartic_sums<float><<<gq, kRedThreads, 0, st()>>>(phin, B.Phi[q ^ 1], B.N, p->partials);
+    else k_quartic_sums<double><<<gq, kRedThreads, 0, st()>>>(phin, B.Phi[q ^ 1], B.N, p->partials);
     prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
-    chk(launch_finalize(p, 2, G(), S_Q, st()));
+    chk(launch_finalize(p, 2, gq, S_Q, st()));
     ctl1(k_c_accept, c(), s());
   }
   cudaError_t precond() {
@@ -566,11 +667,18 @@ struct Seq {
     top();
     chk(precond());
     prof_begin(p, "vec_dir_dots", 80.0 * B.N, 0.0, st());
-    k_dir_dots<<<G(), kRedThreads, 0, st()>>>(B.Pr, B.phi[q], B.r[q], B.r[q ^ 1], B.p[q ^ 1], B.N, p->partials);
+    const int gd = f32 ? wave_grid((const void*)k_dir_dots<float>, B.N)
+                       : wave_grid((const void*)k_dir_dots<double>, B.N);
+    if (f32)
+      k_dir_dots<float><<<gd, kRedThreads, 0, st()>>>(B.Pr, B.phi[q], B.r[q], B.r[q ^ 1], B.p[q ^ 1], B.N,
+                                                      p->partials);
+    else
+      k_dir_dots<double><<<gd, kRedThreads, 0, st()>>>(B.Pr, B.phi[q], B.r[q], B.r[q ^ 1], B.p[q ^ 1], B.N,
+                                                       p->partials);
     prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
-    chk(launch_finalize(p, 7, G(), S_D, st()));
+    chk(launch_finalize(p, 7, gd, S_D, st()));
     ctl1(k_c_dir, c(), s());
     lincomb(B.p[q], B.Pr, Coef{&c()->cp0, 1.0}, B.p[q ^ 1], Coef{&c()->cp1, 1.0}, B.phi[q], Coef{&c()->cp2, 1.0},
             B.Hphi, S_P);
@@ -580,14 +688,19 @@ struct Seq {
     ctl1(k_c_reset2, c(), s());
     hop(B.p[q], B.Hp, -1);
     atkm(SRC_PAIR, reinterpret_cast<const double*>(B.phi[q]), reinterpret_cast<const double*>(B.p[q]), B.Phi1);
-    dots({{B.Hp, B.p[q]}}, S_C);
-    prof_begin(p, "vec_curv_sums", 48.0 * B.N, 0.0, st());
-    k_curv_sums<<<G(), kRedThreads, 0, st()>>>(B.phi[q], B.p[q], B.Phi[q], B.Phi1, ph.beta, ph.lambda, B.N,
-                                                p->partials);
+    prof_begin(p, "vec_curv_sums", 64.0 * B.N, 0.0, st());
+    const int gc = f32 ? wave_grid((const void*)k_curv_sums<float>, B.N)
+                       : wave_grid((const void*)k_curv_sums<double>, B.N);
+    if (f32)
+      k_curv_sums<float><<<gc, kRedThreads, 0, st()>>>(B.Hp, B.phi[q], B.p[q], B.Phi[q], B.Phi1, ph.beta, ph.lambda,
+                                                       B.N, p->partials);
+    else
+      k_curv_sums<double><<<gc, kRedThreads, 0, st()>>>(B.Hp, B.phi[q], B.p[q], B.Phi[q], B.Phi1, ph.beta,
+                                                        ph.lambda, B.N, p->partials);
     prof_end(p, st());
     count_launches(1);
     chk(cudaGetLastError());
-    chk(launch_finalize(p, 3, G(), S_C + 1, st()));
+    chk(launch_finalize(p, 4, gc, S_C, st()));
     ctl1(k_c_step, c(), s());
     trial();
   }
@@ -756,7 +869,7 @@ struct Solver {
       q = 0;
       Seq S = seq(f32);
       const double2* p0 = reinterpret_cast<const double2*>(psi);
-      S.dots({{p0, p0}}, S_N);
+      S.dot(p0, p0, S_N);
       S.ctl1(k_c_init, B->ctl, (const double*)plan->scal);
       S.lincomb(B->phi[0], p0, Coef{&B->ctl->inv0, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr, Coef{nullptr, 0.0},
                 nullptr, S_T);
