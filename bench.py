@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "f64"], default="f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-form", action="store_true", help="skip the FP32-bulk arm")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solve to 1e-8")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "pcg_f64", "pcg_mixed"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture and exit")
@@ -228,6 +230,75 @@ def roofline(stats, peaks):
             "launch_ms": round(per_launch_ms, 4), "launches": dom["launches"]}
 
 
+def timed_steps(B, plan, prm, psi0, precision, warmup, steps, barrier, clk=None):
+    """W warm-up PCG iterations from psi_0, then K timed iterations resuming
+    the same solve, profiled per pass with CUDA events on the plan stream."""
+    import torch
+    psi = psi0.clone()
+    kw = dict(tol_residual=TOL, precision=precision, switch_tol=1e-5)
+    plan.pcg_ground_state(prm, psi, max_iter=warmup, **kw)
+    barrier()
+    if clk:
+        clk.start()
+    launches0 = B.launch_count()
+    plan.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    res = plan.pcg_ground_state(prm, psi, max_iter=steps, resume=True, **kw)
+    ev1.record()
+    barrier()
+    clocks = clk.stop() if clk else None
+    launches = B.launch_count() - launches0
+    stats = plan.kernel_stats()
+    plan.set_profiling(False)
+    return dict(ms=ev0.elapsed_time(ev1), evals=atkm_evals(stats), res=res, stats=stats, clocks=clocks,
+                launches=launches, steps=res["iters"] - warmup, psi=psi)
+
+
+def kernel_table(stats, n=12):
+    top = sorted(stats, key=lambda k: -k["ms_total"])[:n]
+    return [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms_total"], 3),
+             "GB/s": round(k["bytes_total"] / (k["ms_total"] * 1e-3) / 1e9, 1) if k["ms_total"] else None,
+             "GFLOP/s": round(k["flops_total"] / (k["ms_total"] * 1e-3) / 1e9, 1) if k["ms_total"] else None}
+            for k in top]
+
+
+def rel2(a, b) -> float:
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def time_to_tol(B, w):
+    """PCG-ATKM-MG (Algorithm 2; levels N/4, N/2, N) in the precision form
+    from guess (d) on the coarsest grid to residual 1e-8, wall time around
+    the call; plus the FP32-vs-FP64 ATKM error at the final state."""
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import multigrid as MG
+
+    def guess(p, N):
+        return W.initial_guess(W.with_grid(p, N))
+
+    res, sec, psi, grids = MG.solve_mg(w, guess, levels=3, tol=TOL, max_iter=20000,
+                                       precision=B.PRECISION_F32_F64)
+    plan = B.Plan(w.N, w.L, w.n, f32=True)
+    try:
+        phi64 = plan.dipolar_potential_from_psi(psi)
+        phi32 = plan.dipolar_potential_from_psi(psi, f32=True)
+        prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
+        e64 = plan.energy_parts(prm, psi, phi64)
+        e32 = plan.energy_parts(prm, psi, phi32)
+        err = {"Phi_rel_l2_f32_vs_f64": rel2(phi32, phi64),
+               "E_rel_f32_vs_f64": abs(e32["E"] - e64["E"]) / abs(e64["E"]),
+               "mu_rel_f32_vs_f64": abs(e32["mu"] - e64["mu"]) / abs(e64["mu"])}
+    finally:
+        plan.close()
+    out = MG.summary(res, sec, grids)
+    out.update(method="PCG-ATKM-MG, 3 levels, precision form (FP32 bulk, FP64 polish)", tol=TOL,
+               precision_errors_at_final_state=err)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import atkm_workloads as W
@@ -243,35 +314,28 @@ def run_ours(args, rank, world, local_rank):
     prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
     psi0_host = torch.from_numpy(W.initial_guess(w)).pin_memory()
     psi0 = psi0_host.cuda()
-    psi = psi0.clone()
-    kw = dict(tol_residual=TOL, precision=precision, switch_tol=1e-5)
 
     def barrier():
         if dist:
             td.barrier()
         torch.cuda.synchronize()
 
-    # ---- W warm-up iterations start the solve from psi_0
-    plan.pcg_ground_state(prm, psi, max_iter=args.warmup, **kw)
-    # ---- K timed iterations resume it
-    clk = ClockSampler(gpu_index_for(local_rank))
-    barrier()
-    clk.start()
-    launches0 = B.launch_count()
-    plan.set_profiling(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    res = plan.pcg_ground_state(prm, psi, max_iter=args.steps, resume=True, **kw)
-    ev1.record()
-    barrier()
-    clocks = clk.stop()
-    launches = B.launch_count() - launches0
-    stats = plan.kernel_stats()
-    plan.set_profiling(False)
-    ms = ev0.elapsed_time(ev1)
-    evals = atkm_evals(stats)
-    ms_max, evals_all = aggregate_ranks(ms, float(evals), "cuda") if dist else (ms, float(evals))
-    steps_done = res["iters"] - args.warmup
+    # ---- the headline arm: W warm-up + K timed PCG iterations
+    main = timed_steps(B, plan, prm, psi0, precision, args.warmup, args.steps, barrier,
+                       ClockSampler(gpu_index_for(local_rank)))
+    ms_max, evals_all = aggregate_ranks(main["ms"], float(main["evals"]), "cuda") if dist else \
+        (main["ms"], float(main["evals"]))
+
+    # ---- the precision form on the same workload (FP32 bulk, FP64 reductions)
+    pform = None
+    if precision == B.PRECISION_F64 and not args.no_precision_form:
+        mx = timed_steps(B, plan, prm, psi0, B.PRECISION_F32_F64, args.warmup, args.steps, barrier)
+        mms, mev = aggregate_ranks(mx["ms"], float(mx["evals"]), "cuda") if dist else (mx["ms"], float(mx["evals"]))
+        pform = {"value": round(mev / (mms * 1e-3), 2), "unit": UNIT,
+                 "ms_per_step": round(mms / max(mx["steps"], 1), 3), "steps": mx["steps"],
+                 "roofline": roofline(mx["stats"], measured_peaks()), "kernels": kernel_table(mx["stats"]),
+                 "gpu_launches": mx["launches"], "residual_after_steps": mx["res"]["residual"],
+                 "f32_iterations": mx["res"]["f32_iters"]}
 
     # ---- stand-alone ATKM evaluations per second (FP64 and FP32 arithmetic)
     Phi = torch.empty(w.shape, dtype=torch.float64, device="cuda")
@@ -290,9 +354,11 @@ def run_ours(args, rank, world, local_rank):
         standalone[key] = round(n / (e0.elapsed_time(e1) * 1e-3), 1)
 
     # ---- end to end through the public API with host buffers: H2D of psi_0,
-    # W + K iterations from it, D2H of the state and the result struct
+    # W + K iterations from it, D2H of the state
     barrier()
+    psi = torch.empty_like(psi0)
     host_out = torch.empty_like(psi0_host).pin_memory()
+    kw = dict(tol_residual=TOL, precision=precision, switch_tol=1e-5)
     plan.set_profiling(True)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record()
@@ -306,9 +372,17 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = f0.elapsed_time(f1)
     e2e_evals = atkm_evals(e2e_stats)
     nbytes = psi0_host.numel() * psi0_host.element_size()
-    return dict(ms=ms_max, evals=evals_all, steps=steps_done, res=res, standalone=standalone,
+    plan.close()
+
+    # ---- time to the residual tolerance (single process only: replicas would
+    # only repeat it)
+    ttt = None
+    if not args.no_time_to_tol and world == 1:
+        ttt = time_to_tol(B, w)
+    return dict(ms=ms_max, evals=evals_all, steps=main["steps"], res=main["res"], standalone=standalone,
                 e2e_value=e2e_evals * world / (e2e_ms * 1e-3), nbytes=nbytes,
-                roof=roofline(stats, measured_peaks()), stats=stats, clocks=clocks, launches=launches)
+                roof=roofline(main["stats"], measured_peaks()), stats=main["stats"], clocks=main["clocks"],
+                launches=main["launches"], pform=pform, ttt=ttt)
 
 
 def profile_case(case: str):
@@ -383,11 +457,7 @@ def main():
     if rank == 0:
         res = out["res"]
         value = out["evals"] / (out["ms"] * 1e-3)
-        kernels = sorted(out["stats"], key=lambda k: -k["ms_total"])[:24]
-        ktable = [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms_total"], 3),
-                   "GB/s": round(k["bytes_total"] / (k["ms_total"] * 1e-3) / 1e9, 1) if k["ms_total"] else None,
-                   "GFLOP/s": round(k["flops_total"] / (k["ms_total"] * 1e-3) / 1e9, 1) if k["ms_total"] else None}
-                  for k in kernels]
+        ktable = kernel_table(out["stats"], 24)
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": out["steps"],
             "warmup": args.warmup, "ms_per_step": round(out["ms"] / max(out["steps"], 1), 3),
@@ -402,9 +472,14 @@ def main():
             "standalone_atkm_evals_per_s": out["standalone"],
             "roofline": out["roof"], "kernels": ktable, "clocks": out["clocks"],
             "gpu_launches": out["launches"],
-            "e2e": {"value": round(out["e2e_value"], 2), "unit": UNIT, "h2d_bytes_per_step": out["nbytes"],
-                    "d2h_bytes_per_step": out["nbytes"], "note": "one H2D of psi_0 and one D2H of the state around warmup+steps iterations"},
+            "e2e": {"value": round(out["e2e_value"], 2), "unit": UNIT,
+                    "h2d_bytes_per_step": round(out["nbytes"] / (args.warmup + args.steps)),
+                    "d2h_bytes_per_step": round(out["nbytes"] / (args.warmup + args.steps)),
+                    "note": "pcg_ground_state from pinned host psi_0: one H2D of psi_0, warmup+steps iterations, "
+                            "one D2H of the state, all inside the timed region (bytes per step = bytes / iterations)"},
             "cpu_baseline": cpu,
+            "precision_form": out["pform"],
+            "time_to_1e-8": out["ttt"],
         }
         print(json.dumps(line))
     if dist:

@@ -505,6 +505,7 @@ template <typename R, bool RED> struct OpHY : OpBase<-1, true, RED ? 2 : 0, fals
 // Reductions: kin_z, sum V|f|^2, sum |f|^4, sum Phi |f|^2, sum Re(Hf conj f), sum |f|^2.
 template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, false> {
   const double2* f; const double2* phi; const double* Phi; const cx<R>* acc; double2* Hf; Cst<R> c; PhysR<R> ph;
+  bool same = false;  // f == phi (H phi): phi is not read a second time
   __device__ bool valid(int, int x) const { return x < c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)pos * c.Ny + o) * c.Nx + x]); }
   __device__ void spectral(int, int, int k, cx<R>& v, R* a) const {
@@ -518,7 +519,8 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
     const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
     const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
-    const cx<R> fv = from64<R>(f[idx]), pv = from64<R>(phi[idx]);
+    const cx<R> fv = from64<R>(f[idx]);
+    const cx<R> pv = same ? fv : from64<R>(phi[idx]);
     const R Pd = tor<R>(Phi[idx]);
     const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
     const cx<R> kin = add<R>(acc[idx], v);

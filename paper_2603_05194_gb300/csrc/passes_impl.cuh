@@ -141,12 +141,14 @@ cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double
     const char* n = nm<R>("H_z_f64", "H_z_f32");
     if (red) {
       OpHZ<R, true> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
+      op.same = fin == pin;
       op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
-      ATKM_RUN(n, 56 * N + N * s, fl, op, p->fN[2], pg);
+      ATKM_RUN(n, (op.same ? 40 : 56) * N + N * s, fl, op, p->fN[2], pg);
       if ((e = launch_finalize(p, 6, pg.grid.x * pg.grid.y, red_slot + 4, st)) != cudaSuccess) return e;
     } else {
       OpHZ<R, false> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
-      ATKM_RUN(n, 56 * N + N * s, fl, op, p->fN[2], pg);
+      op.same = fin == pin;
+      ATKM_RUN(n, (op.same ? 40 : 56) * N + N * s, fl, op, p->fN[2], pg);
     }
   }
   return cudaSuccess;
