@@ -191,6 +191,12 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
 #define ATKM_PRECISION_F32_F64 1  /* complex64 FFT/ATKM/H/P until switch_tol, two exhausted
                                      halving loops, or 400 iterations without halving the
                                      best FP32 residual; then FP64                     */
+#define ATKM_PRECISION_F32_SPLIT 2 /* as ATKM_PRECISION_F32_F64, and after the hand-over the
+                                     operators that only shape the search direction and
+                                     the step-size model (P r, H p and the ATKM of
+                                     Re(conj(phi) p)) stay complex64; H phi (residual,
+                                     mu), the trial-energy ATKM, every reduction, the
+                                     retraction and the stop test are FP64             */
 
 typedef struct atkm_pcg_opts {
   double tol_residual;  /* stop when ||H phi - mu phi|| <= tol_residual (e.g. 1e-8)    */

@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED_SIZE", 3: "ERR_OOM", 
 ATKM_PLAN_F32 = 1
 PRECISION_F64 = 0
 PRECISION_F32_F64 = 1
+PRECISION_F32_SPLIT = 2
 
 
 class AtkmError(RuntimeError):

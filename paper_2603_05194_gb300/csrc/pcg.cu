@@ -488,11 +488,12 @@ struct PcgBuffers {
   cudaStream_t st = nullptr; // plan-owned stream (capturable)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // graphs: [f32][parity][kind: 0 iteration, 1 halve+trial, 2 best+trial]
-  cudaGraphExec_t gx[2][2][3] = {};
-  int gnodes[2][2][3] = {};
-  bool seen[2][2][3] = {};
-  bool gprof[2][2][3] = {};                 // captured with profiling events
-  std::vector<ProfRec> grecs[2][2][3];      // those events
+  // captured graphs per [form: FP64, FP32, FP64 with FP32 auxiliaries][parity][kind]
+  cudaGraphExec_t gx[3][2][3] = {};
+  int gnodes[3][2][3] = {};
+  bool seen[3][2][3] = {};
+  bool gprof[3][2][3] = {};                 // captured with profiling events
+  std::vector<ProfRec> grecs[3][2][3];      // those events
   const std::vector<ProfRec>* last = nullptr;  // records of the last replay
   bool graphs_ok = true;
   Phys gphys{};
@@ -516,7 +517,7 @@ static void drop_graph(PcgBuffers* b, int f, int q, int k) {
 }
 
 static void destroy_graphs(PcgBuffers* b) {
-  for (int f = 0; f < 2; ++f)
+  for (int f = 0; f < 3; ++f)
     for (int q = 0; q < 2; ++q)
       for (int k = 0; k < 3; ++k) drop_graph(b, f, q, k);
   b->last = nullptr;
@@ -574,6 +575,9 @@ struct Seq {
   bool f32;
   int q;  // buffer parity: phi = B.phi[q], trial into B.phi[q ^ 1]
   cudaError_t err = cudaSuccess;
+  // FP64 phase of the split form: the operators that only shape the search
+  // direction and the step-size model (P r, H p, the pair ATKM) run in FP32.
+  bool aux32 = false;
   Ctl* c() const { return B.ctl; }
   const double* s() const { return p->scal; }
   cudaStream_t st() const { return B.st; }
@@ -604,15 +608,17 @@ struct Seq {
     count_launches(2);
     chk(cudaGetLastError());
   }
-  void atkm(int mode, const double* a, const double* b, double* o) {
-    chk(f32 ? launch_atkm<float>(p, mode, a, b, o, st()) : launch_atkm<double>(p, mode, a, b, o, st()));
+  void atkm(int mode, const double* a, const double* b, double* o, bool aux = false) {
+    const bool use32 = f32 || (aux && aux32);
+    chk(use32 ? launch_atkm<float>(p, mode, a, b, o, st()) : launch_atkm<double>(p, mode, a, b, o, st()));
   }
-  void hop(const double2* f, double2* o, int red) {
+  void hop(const double2* f, double2* o, int red, bool aux = false) {
     const double* fp = reinterpret_cast<const double*>(f);
     const double* pp = reinterpret_cast<const double*>(B.phi[q]);
     double* op = reinterpret_cast<double*>(o);
-    chk(f32 ? launch_H<float>(p, ph, fp, pp, B.Phi[q], op, red, st())
-            : launch_H<double>(p, ph, fp, pp, B.Phi[q], op, red, st()));
+    const bool use32 = f32 || (aux && aux32);
+    chk(use32 ? launch_H<float>(p, ph, fp, pp, B.Phi[q], op, red, st())
+              : launch_H<double>(p, ph, fp, pp, B.Phi[q], op, red, st()));
   }
   template <typename K, typename... A> void ctl1(K kernel, A... args) {
     kernel<<<1, 1, 0, st()>>>(args...);
@@ -659,8 +665,8 @@ struct Seq {
     const double* r = reinterpret_cast<const double*>(B.r[q]);
     const double* phi = reinterpret_cast<const double*>(B.phi[q]);
     double* Pr = reinterpret_cast<double*>(B.Pr);
-    return f32 ? launch_precond<float>(p, ph, &c()->alpha, r, phi, B.Phi[q], Pr, st())
-               : launch_precond<double>(p, ph, &c()->alpha, r, phi, B.Phi[q], Pr, st());
+    return (f32 || aux32) ? launch_precond<float>(p, ph, &c()->alpha, r, phi, B.Phi[q], Pr, st())
+                          : launch_precond<double>(p, ph, &c()->alpha, r, phi, B.Phi[q], Pr, st());
   }
   // A whole iteration: Steps 2-4 up to the first trial.
   void iteration() {
@@ -686,8 +692,8 @@ struct Seq {
     lincomb(B.p[q], B.Pr, Coef{nullptr, -1.0}, B.phi[q], Coef{&c()->b, 1.0}, nullptr, Coef{nullptr, 0.0}, B.Hphi, S_P,
             &c()->redo);
     ctl1(k_c_reset2, c(), s());
-    hop(B.p[q], B.Hp, -1);
-    atkm(SRC_PAIR, reinterpret_cast<const double*>(B.phi[q]), reinterpret_cast<const double*>(B.p[q]), B.Phi1);
+    hop(B.p[q], B.Hp, -1, true);
+    atkm(SRC_PAIR, reinterpret_cast<const double*>(B.phi[q]), reinterpret_cast<const double*>(B.p[q]), B.Phi1, true);
     prof_begin(p, "vec_curv_sums", 64.0 * B.N, 0.0, st());
     const int gc = f32 ? wave_grid((const void*)k_curv_sums<float>, B.N)
                        : wave_grid((const void*)k_curv_sums<double>, B.N);
@@ -721,7 +727,7 @@ struct Seq {
 static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   PcgBuffers& B = S.B;
   atkm_plan* p = S.p;
-  const int fi = S.f32 ? 1 : 0;
+  const int fi = S.f32 ? 1 : (S.aux32 ? 2 : 0);
   const bool prof = p->prof != nullptr;
   B.last = nullptr;
   if (!use_graphs || !B.graphs_ok) {
@@ -800,7 +806,7 @@ struct Solver {
   PcgBuffers* B = nullptr;
   cudaStream_t caller = nullptr;
   Phys ph{};
-  bool mixed = false, use_graphs = true, f32 = false, began = false;
+  bool mixed = false, split = false, use_graphs = true, f32 = false, began = false;
   int q = 0, n = 0, n_start = 0, caps = 0, status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0, logc = 0;
   int f32_best_n = 0, early_code = ATKM_OK;
   double linf = INFINITY, f32_best = INFINITY;
@@ -812,7 +818,11 @@ struct Solver {
   void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
   bool done() const { return st == DONE || err != cudaSuccess; }
   Ctl& H() { return *B->ctl_h; }
-  Seq seq(bool is32) { return Seq{plan, *B, ph, is32, q}; }
+  Seq seq(bool is32) {
+    Seq S{plan, *B, ph, is32, q};
+    S.aux32 = split && !is32;
+    return S;
+  }
   void fetch_async() { chk(cudaMemcpyAsync(B->ctl_h, B->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, B->st)); }
   void set_scalar(double* dst, double v) {
     k_set_scalar<<<1, 1, 0, B->st>>>(dst, v);
@@ -826,7 +836,8 @@ struct Solver {
     if (!plan || !prm || !opts || !psi || !out) return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: NULL argument");
     if (!(opts->tol_residual >= 0.0) || opts->max_iter < 0 || opts->max_halvings < 0)
       return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: bad options");
-    mixed = opts->precision_mode == ATKM_PRECISION_F32_F64;
+    split = opts->precision_mode == ATKM_PRECISION_F32_SPLIT;
+    mixed = opts->precision_mode == ATKM_PRECISION_F32_F64 || split;
     if (opts->precision_mode != ATKM_PRECISION_F64 && !mixed)
       return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: unknown precision_mode");
     if (mixed && !(plan->flags & ATKM_PLAN_F32))

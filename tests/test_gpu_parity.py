@@ -185,13 +185,34 @@ def test_pcg_invariants_along_run(lib):
     assert abs(h3 * float(torch.sum(torch.abs(psi) ** 2)) - 1.0) < 1e-13
 
 
-def test_mixed_precision_reaches_fp64_energy(lib):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_reaches_fp64_energy(lib, precision):
+    """FP32 bulk then FP64 polish (1), and the split polish with FP32
+    direction/step-model operators (2): the same FP64 ground state."""
     w = W.CONFIGS["cfg1_32x32x16"]
     _, _, r64 = _run_pair(lib, w, 400)
-    _, _, rmx = _run_pair(lib, w, 400, precision=1)
+    _, _, rmx = _run_pair(lib, w, 400, precision=precision)
     assert rmx["status"] == 0 and rmx["residual"] <= 1e-8
     assert rmx["f32_iters"] > 0
     assert abs(rmx["E"] - r64["E"]) <= 1e-9 * abs(r64["E"])
+    assert abs(rmx["mu"] - r64["mu"]) <= 1e-9 * abs(r64["mu"])
+
+
+def test_split_precision_matches_oracle_ground_state(lib):
+    """The split form on a tilted-dipole anisotropic case against the FP64
+    oracle's Algorithm 1: E and mu within 1e-10 relative."""
+    N, L, n = (24, 20, 12), (5.0, 4.0, 1.2), (0.6, 0.0, 0.8)
+    gamma, beta, lam, Om = (1.0, 1.3, 6.0), 40.0, -12.0, 0.3
+    psi0 = W.guess_phi_d(N, L, gamma, Om)
+    ref = O.pcg_ground_state(O.Plan(N, L, n), O.Params(gamma, beta, lam, Om), psi0,
+                             O.PcgOptions(tol_residual=1e-9, max_iter=600))
+    plan = lib.Plan(N, L, n, f32=True)
+    psi = dev(psi0)
+    r = plan.pcg_ground_state(lib.make_params(gamma, beta, lam, Om), psi, tol_residual=1e-9, max_iter=600,
+                              precision=2)
+    assert ref.status == O.OK and r["status"] == 0
+    assert abs(r["E"] - ref.parts["E"]) <= 1e-10 * abs(ref.parts["E"])
+    assert abs(r["mu"] - ref.mu) <= 1e-10 * abs(ref.mu)
 
 
 def test_f32_atkm_close_to_oracle(lib):
