@@ -182,7 +182,11 @@ FP64_PEAK_GFLOPS = 1255.0
 # passes that can be the dominant kernel, from one ncu capture of the current
 # kernels on this workload (the profile file gives the command).  A kernel not
 # listed here reports traffic null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "atkm_z_f64": {"bytes": 271659264.0, "profile": "profiles/atkm_z_f64_256x256x64.md"},
+    "H_z_f32": {"bytes": 172601344.0,
+                "profile": "profiles/pcg_mixed_kernels_256x256x64.md (the H phi launch with energy sums)"},
+}
 
 
 # ------------------------------------------------------------------ ours
