@@ -51,6 +51,7 @@ typedef struct atkm_plan atkm_plan;
 /* Plan flags (bit set). */
 #define ATKM_PLAN_F64 0u   /* FP64 workspaces (always present)                  */
 #define ATKM_PLAN_F32 1u   /* also allocate complex64 workspaces for the _f32 calls */
+#define ATKM_PLAN_DF32 2u  /* also keep a double-word copy of U0 for the _df32 calls  */
 
 /*
  * atkm_plan_create -- grid, box, dipole axis; precomputes the truncated-kernel
@@ -59,7 +60,7 @@ typedef struct atkm_plan atkm_plan;
  *   N[3]  grid sizes (N_x, N_y, N_z), see conventions.
  *   L[3]  box half-lengths, each > 0 and finite.
  *   n[3]  dipole orientation; | |n| - 1 | must be <= 1e-12 (Eq. (DDI-3D)).
- *   flags ATKM_PLAN_F64 or ATKM_PLAN_F32.
+ *   flags ATKM_PLAN_F64, or any of ATKM_PLAN_F32 and ATKM_PLAN_DF32.
  * Builds, in FP64 on the device, U0(nu) = int_{D_2L} e^{-i nu.y}/(4 pi|y|) dy on
  * the nonnegative frequency octant of the twofold-padded grid (Eq. (FUk)),
  * from which the dipolar multiplier K = -1 + 3 (n.nu)^2 U0 is formed on the
@@ -142,6 +143,15 @@ int dipolar_potential_from_pair(atkm_plan* plan, const double* a, const double* 
  * and rounded per use.  Relative error ~1e-6 of max|Phi|. */
 int dipolar_potential_from_psi_f32(atkm_plan* plan, const double* psi, double* phi, void* stream);
 
+/* Double-word variant of dipolar_potential_from_psi (plan needs
+ * ATKM_PLAN_DF32): same FP64 interface and the same padded convolution
+ * (§2.2), with every FFT pass in double-FP32 arithmetic -- each value is an
+ * unevaluated sum of two binary32 numbers, about 48 significant bits --
+ * computed on the FP32 pipe, which runs about 57 times the binary64 rate on
+ * this GPU.  Uses the FP64 workspaces.  Relative error about 1e-14 of
+ * ||Phi|| (the FP64 call reaches about 1e-15). */
+int dipolar_potential_from_psi_df32(atkm_plan* plan, const double* psi, double* phi, void* stream);
+
 /* Physical parameters of the energy (Eqs. (DipGPE0), (Vpoten)). */
 typedef struct atkm_params {
   double gamma[3]; /* trap frequencies gamma_x, gamma_y, gamma_z */
@@ -197,6 +207,13 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
                                      Re(conj(phi) p)) stay complex64; H phi (residual,
                                      mu), the trial-energy ATKM, every reduction, the
                                      retraction and the stop test are FP64             */
+#define ATKM_PRECISION_DF32_SPLIT 3 /* as ATKM_PRECISION_F32_SPLIT, with H phi and the
+                                     trial-energy ATKM of the polish in double-FP32
+                                     arithmetic (about 48 bits, on the FP32 pipe;
+                                     plan needs ATKM_PLAN_F32 | ATKM_PLAN_DF32); the
+                                     reductions and the retraction stay FP64, and the
+                                     stop test's residual is formed from the double-
+                                     word H phi (error about 1e-14 relative)           */
 
 typedef struct atkm_pcg_opts {
   double tol_residual;  /* stop when ||H phi - mu phi|| <= tol_residual (e.g. 1e-8)    */

@@ -26,9 +26,11 @@ ATKM_ERR_TIMEOUT = 8
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED_SIZE", 3: "ERR_OOM", 4: "ERR_CUDA",
                 5: "NOT_CONVERGED", 6: "STAGNATED", 7: "ERR_NAN", 8: "ERR_TIMEOUT"}
 ATKM_PLAN_F32 = 1
+ATKM_PLAN_DF32 = 2
 PRECISION_F64 = 0
 PRECISION_F32_F64 = 1
 PRECISION_F32_SPLIT = 2
+PRECISION_DF32_SPLIT = 3
 
 
 class AtkmError(RuntimeError):
@@ -93,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "dipolar_potential_from_psi": (ip, [vp, vp, vp, vp]),
         "dipolar_potential_from_pair": (ip, [vp, vp, vp, vp, vp]),
         "dipolar_potential_from_psi_f32": (ip, [vp, vp, vp, vp]),
+        "dipolar_potential_from_psi_df32": (ip, [vp, vp, vp, vp]),
         "apply_H": (ip, [vp, C.POINTER(Params), vp, vp, vp, vp, vp]),
         "atkm_energy_parts": (ip, [vp, C.POINTER(Params), vp, vp, C.POINTER(Energy), vp]),
         "apply_preconditioner": (ip, [vp, C.POINTER(Params), C.c_double, vp, vp, vp, vp, vp]),
@@ -307,7 +310,7 @@ def make_params(gamma, beta, lam, Omega) -> Params:
 class Plan:
     """Owning handle of an atkm_plan (grid, box, dipole axis, multiplier)."""
 
-    def __init__(self, N, L, n, f32: bool = False, stream=None):
+    def __init__(self, N, L, n, f32: bool = False, stream=None, df32: bool = False):
         lib = load_library()
         self.N = tuple(int(v) for v in N)
         self.L = tuple(float(v) for v in L)
@@ -317,7 +320,8 @@ class Plan:
         Na = (C.c_int * 3)(*self.N)
         La = (C.c_double * 3)(*self.L)
         na = (C.c_double * 3)(*self.n)
-        code = lib.atkm_plan_create(C.byref(self._h), Na, La, na, ATKM_PLAN_F32 if f32 else 0, _stream(stream))
+        flags = (ATKM_PLAN_F32 if f32 else 0) | (ATKM_PLAN_DF32 if df32 else 0)
+        code = lib.atkm_plan_create(C.byref(self._h), Na, La, na, flags, _stream(stream))
         if code != ATKM_OK:
             raise AtkmError(code, lib.atkm_last_error_string(None).decode())
         self._lib = lib
@@ -372,9 +376,10 @@ class Plan:
                                                 _ptr(out, torch.float64, self.shape, "phi"), _stream(stream)))
         return out
 
-    def dipolar_potential_from_psi(self, psi, out=None, stream=None, f32=False):
+    def dipolar_potential_from_psi(self, psi, out=None, stream=None, f32=False, df32=False):
         out = torch.empty(self.shape, dtype=torch.float64, device="cuda") if out is None else out
-        fn = self._lib.dipolar_potential_from_psi_f32 if f32 else self._lib.dipolar_potential_from_psi
+        fn = (self._lib.dipolar_potential_from_psi_f32 if f32 else
+              self._lib.dipolar_potential_from_psi_df32 if df32 else self._lib.dipolar_potential_from_psi)
         self._check(fn(self._h, _ptr(psi, torch.complex128, self.shape, "psi"),
                        _ptr(out, torch.float64, self.shape, "phi"), _stream(stream)))
         return out

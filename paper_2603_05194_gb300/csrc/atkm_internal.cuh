@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/atkm.h"
+#include "df32.cuh"
 
 namespace atkm {
 
@@ -17,6 +18,7 @@ namespace atkm {
 template <typename R> struct CT;
 template <> struct CT<double> { using c = double2; };
 template <> struct CT<float> { using c = float2; };
+template <> struct CT<df> { using c = cdf; };
 template <typename R> using cx = typename CT<R>::c;
 
 template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
@@ -61,6 +63,13 @@ template <> __device__ __forceinline__ float tor<float>(double v) { return d2f_b
 template <typename R> __device__ __forceinline__ double tod(R v);
 template <> __device__ __forceinline__ double tod<double>(double v) { return v; }
 template <> __device__ __forceinline__ double tod<float>(float v) { return f2d_bits(v); }
+// binary64 <-> double-word: the leading binary32 part from the bit layout, the
+// trailing part from the exact binary64 remainder (one binary64 subtraction).
+template <> __device__ __forceinline__ df tor<df>(double v) {
+  const float h = d2f_bits(v);
+  return df(h, d2f_bits(v - f2d_bits(h)));
+}
+template <> __device__ __forceinline__ double tod<df>(df v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
 
 template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
 template <typename R> __device__ __forceinline__ cx<R> sub(cx<R> a, cx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
@@ -93,6 +102,7 @@ constexpr int kMaxElems = 4096;    // complex elements per CTA tile (upper bound
 template <typename R> struct TileElems;
 template <> struct TileElems<double> { static constexpr int value = 2048; };
 template <> struct TileElems<float> { static constexpr int value = 4096; };
+template <> struct TileElems<df> { static constexpr int value = 2048; };
 constexpr int kMaxStages = 12;
 constexpr int kMaxLen = 2048;     // longest (padded) line; <= TileElems<double>
 
@@ -102,11 +112,13 @@ struct FftLen {
   int radix[kMaxStages];
   const double2* tw64;  // e^{-2 pi i m / L}, m = 0..L-1
   const float2* tw32;
+  const cdf* twdf;      // the binary64 table split into double-word
 };
 
 template <typename R> __host__ __device__ __forceinline__ const cx<R>* tw_table(const FftLen& f);
 template <> __host__ __device__ __forceinline__ const double2* tw_table<double>(const FftLen& f) { return f.tw64; }
 template <> __host__ __device__ __forceinline__ const float2* tw_table<float>(const FftLen& f) { return f.tw32; }
+template <> __host__ __device__ __forceinline__ const cdf* tw_table<df>(const FftLen& f) { return f.twdf; }
 template <typename R> inline const cx<R>* tw_table_host(const FftLen& f) { return tw_table<R>(f); }
 
 // Exact trigonometric constants of the small DFTs (closed forms in radicals).
@@ -331,6 +343,8 @@ struct atkm_plan {
   float2* tw32;
   double* U0;          // octant (Nz+1)(Ny+1)(Nx+1)
   float* U0f;          // FP32 copy of U0 (FP32 workspaces only)
+  atkm::df* U0d;       // double-word copy of U0 (ATKM_PLAN_DF32 only)
+  atkm::cdf* twdf;     // double-word twiddle pool
   double2* W1;         // [Nz][Ny][XS] half spectrum in x
   double2* W2;         // [Nz][My][XS]
   double2* T1;         // [Nz][Ny][Nx]

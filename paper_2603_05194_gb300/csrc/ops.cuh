@@ -15,6 +15,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "atkm_internal.cuh"
 
 namespace atkm {
@@ -56,11 +58,13 @@ template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R
 template <typename R> __device__ __forceinline__ R rsq(R v);
 template <> __device__ __forceinline__ double rsq<double>(double v) { return rsqrt(v); }
 template <> __device__ __forceinline__ float rsq<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ df rsq<df>(df v) { return df_rsqrt(v); }
 
 // ------------------------------------------------------------- FastFft
 template <typename R> struct SmemShift;  // one pad element per 128 bytes
 template <> struct SmemShift<double> { static constexpr int value = 3; };
 template <> struct SmemShift<float> { static constexpr int value = 4; };
+template <> struct SmemShift<df> { static constexpr int value = 3; };
 
 constexpr int kFastElems = 2048;  // elements per CTA (256 threads x 8)
 
@@ -147,8 +151,13 @@ template <typename R, int NR>
 __device__ __forceinline__ void reduce_out(R (&acc)[NR], double* part, int pstride) {
   if constexpr (sizeof(R) == 4) {
     block_reduce_store_f32<NR>(acc, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
-  } else {
+  } else if constexpr (std::is_same<R, double>::value) {
     block_reduce_store<NR>(acc, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
+  } else {  // double-word partials: widened per thread, FP64 beyond
+    double d[NR];
+#pragma unroll
+    for (int s = 0; s < NR; ++s) d[s] = tod<R>(acc[s]);
+    block_reduce_store<NR>(d, part, pstride, blockIdx.y * gridDim.x + blockIdx.x);
   }
 }
 

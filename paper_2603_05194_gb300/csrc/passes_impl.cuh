@@ -11,17 +11,24 @@ namespace atkm {
 template <typename R> inline cx<R>* ws1(atkm_plan* p);
 template <> inline double2* ws1<double>(atkm_plan* p) { return p->W1; }
 template <> inline float2* ws1<float>(atkm_plan* p) { return p->W1f; }
+// double-word passes reuse the FP64 workspaces (16-byte complex elements as well)
+template <> inline cdf* ws1<df>(atkm_plan* p) { return reinterpret_cast<cdf*>(p->W1); }
 template <typename R> inline cx<R>* ws2(atkm_plan* p);
 template <> inline double2* ws2<double>(atkm_plan* p) { return p->W2; }
 template <> inline float2* ws2<float>(atkm_plan* p) { return p->W2f; }
+template <> inline cdf* ws2<df>(atkm_plan* p) { return reinterpret_cast<cdf*>(p->W2); }
 template <typename R> inline cx<R>* ws3(atkm_plan* p);
 template <> inline double2* ws3<double>(atkm_plan* p) { return p->T1; }
 template <> inline float2* ws3<float>(atkm_plan* p) { return p->T1f; }
+template <> inline cdf* ws3<df>(atkm_plan* p) { return reinterpret_cast<cdf*>(p->T1); }
 template <typename R> inline const R* u0tab(atkm_plan* p);
 template <> inline const double* u0tab<double>(atkm_plan* p) { return p->U0; }
 template <> inline const float* u0tab<float>(atkm_plan* p) { return p->U0f; }
+template <> inline const df* u0tab<df>(atkm_plan* p) { return p->U0d; }
 
-template <typename R> inline const char* nm(const char* d, const char* f) { return sizeof(R) == 8 ? d : f; }
+template <typename R> inline const char* nm(const char* d, const char* f, const char* w) {
+  return std::is_same<R, double>::value ? d : (std::is_same<R, float>::value ? f : w);
+}
 inline double fftflops(double n) { return 5.0 * n * log2(n); }
 
 #define ATKM_RUN(NAME, BYTES, FLOPS, OP, FLEN, PG)              \
@@ -51,7 +58,7 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
   const long nl = (long)g.Nz * g.Ny;
   // x forward (real data: complex FFT of length Nx + post-twist)
   const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
-  const char* nx = nm<R>("atkm_x_fwd_f64", "atkm_x_fwd_f32");
+  const char* nx = nm<R>("atkm_x_fwd_f64", "atkm_x_fwd_f32", "atkm_x_fwd_df");
   if (mode == SRC_RHO) {
     OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
     ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
@@ -66,7 +73,7 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
   const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
   {
     OpAtkmYF<R> op; op.W1 = W1; op.W2 = W2; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32"), 3 * H1 * s, fy, op, p->fM[1], gy);
+    ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32", "atkm_y_fwd_df"), 3 * H1 * s, fy, op, p->fM[1], gy);
   }
   // z forward * K_sym * inverse
   {
@@ -74,24 +81,26 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
     op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
     op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
     const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Xh, g.My);
-    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32"), 4 * H1 * s + u0b, fz, op, p->fM[2], pg);
+    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * H1 * s + u0b, fz, op, p->fM[2], pg);
   }
   // y inverse
   {
     OpAtkmYI<R> op; op.W2 = W2; op.W1 = W1; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32"), 3 * H1 * s, fy, op, p->fM[1], gy);
+    ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32", "atkm_y_inv_df"), 3 * H1 * s, fy, op, p->fM[1], gy);
   }
   // x inverse (C2R) + crop
   {
     OpAtkmXI<R> op; op.W1 = W1; op.phi = phi; op.twM = twM; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32"), H1 * s + 8 * N, fx, op, p->fN[0], gx);
+    ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32", "atkm_x_inv_df"), H1 * s + 8 * N, fx, op, p->fN[0], gx);
   }
   return cudaSuccess;
 }
 
+// One axis pass of H_phi f (a function of its own so that heavy
+// instantiations can be compiled in separate translation units).
 template <typename R>
-cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double* phi, const double* Phi, double* Hf,
-                     int red_slot, cudaStream_t st) {
+cudaError_t h_pass_x(atkm_plan* p, const Phys& ph, const double* f, const double* phi, const double* Phi, double* Hf,
+                    int red_slot, cudaStream_t st) {
   const Geo& g = p->g;
   cx<R>* acc = ws3<R>(p);
   if (!acc) return cudaErrorInvalidValue;
@@ -104,11 +113,12 @@ cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double
   const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
   const long nl = (long)g.Nz * g.Ny;
   cudaError_t e;
+  (void)pin; (void)out; (void)nl; (void)pr; (void)e;
   // x
   {
     const PassGrid pg = pass_grid<R>(g.Nx, true, nl, 0, 0);
     const double fl = 2.0 * nl * fftflops(g.Nx);
-    const char* n = nm<R>("H_x_f64", "H_x_f32");
+    const char* n = nm<R>("H_x_f64", "H_x_f32", "H_x_df");
     if (red) {
       OpHX<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
       op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
@@ -119,11 +129,30 @@ cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double
       ATKM_RUN(n, 16 * N + N * s, fl, op, p->fN[0], pg);
     }
   }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t h_pass_y(atkm_plan* p, const Phys& ph, const double* f, const double* phi, const double* Phi, double* Hf,
+                    int red_slot, cudaStream_t st) {
+  const Geo& g = p->g;
+  cx<R>* acc = ws3<R>(p);
+  if (!acc) return cudaErrorInvalidValue;
+  const bool red = red_slot >= 0;
+  const Cst<R> c = make_cst<R>(g);
+  const PhysR<R> pr = make_physr<R>(ph);
+  const double2* fin = reinterpret_cast<const double2*>(f);
+  const double2* pin = reinterpret_cast<const double2*>(phi);
+  double2* out = reinterpret_cast<double2*>(Hf);
+  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const long nl = (long)g.Nz * g.Ny;
+  cudaError_t e;
+  (void)pin; (void)out; (void)nl; (void)pr; (void)e;
   // y
   {
     const PassGrid pg = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
     const double fl = 2.0 * g.Nz * g.Nx * fftflops(g.Ny);
-    const char* n = nm<R>("H_y_f64", "H_y_f32");
+    const char* n = nm<R>("H_y_f64", "H_y_f32", "H_y_df");
     if (red) {
       OpHY<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
       op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
@@ -134,11 +163,30 @@ cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double
       ATKM_RUN(n, 16 * N + 2 * N * s, fl, op, p->fN[1], pg);
     }
   }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t h_pass_z(atkm_plan* p, const Phys& ph, const double* f, const double* phi, const double* Phi, double* Hf,
+                    int red_slot, cudaStream_t st) {
+  const Geo& g = p->g;
+  cx<R>* acc = ws3<R>(p);
+  if (!acc) return cudaErrorInvalidValue;
+  const bool red = red_slot >= 0;
+  const Cst<R> c = make_cst<R>(g);
+  const PhysR<R> pr = make_physr<R>(ph);
+  const double2* fin = reinterpret_cast<const double2*>(f);
+  const double2* pin = reinterpret_cast<const double2*>(phi);
+  double2* out = reinterpret_cast<double2*>(Hf);
+  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
+  const long nl = (long)g.Nz * g.Ny;
+  cudaError_t e;
+  (void)pin; (void)out; (void)nl; (void)pr; (void)e;
   // z + pointwise
   {
     const PassGrid pg = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
     const double fl = 2.0 * g.Ny * g.Nx * fftflops(g.Nz);
-    const char* n = nm<R>("H_z_f64", "H_z_f32");
+    const char* n = nm<R>("H_z_f64", "H_z_f32", "H_z_df");
     if (red) {
       OpHZ<R, true> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
       op.same = fin == pin;
@@ -152,6 +200,15 @@ cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double
     }
   }
   return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_H(atkm_plan* p, const Phys& ph, const double* f, const double* phi, const double* Phi, double* Hf,
+                     int red_slot, cudaStream_t st) {
+  cudaError_t e = h_pass_x<R>(p, ph, f, phi, Phi, Hf, red_slot, st);
+  if (e == cudaSuccess) e = h_pass_y<R>(p, ph, f, phi, Phi, Hf, red_slot, st);
+  if (e == cudaSuccess) e = h_pass_z<R>(p, ph, f, phi, Phi, Hf, red_slot, st);
+  return e;
 }
 
 template <typename R>
@@ -171,24 +228,24 @@ cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev
   {
     OpPXF<R> op; op.r = reinterpret_cast<const double2*>(r); op.phi = reinterpret_cast<const double2*>(phi);
     op.Phi = Phi; op.Wk = Wk; op.c = c; op.ph = pr; op.alpha = alpha_dev;
-    ATKM_RUN(nm<R>("P_x_fwd_f64", "P_x_fwd_f32"), 40 * N + N * s, fx, op, p->fN[0], gx);
+    ATKM_RUN(nm<R>("P_x_fwd_f64", "P_x_fwd_f32", "P_x_fwd_df"), 40 * N + N * s, fx, op, p->fN[0], gx);
   }
   {
     OpPY<R, -1> op; op.Wk = Wk; op.c = c;
-    ATKM_RUN(nm<R>("P_y_f64", "P_y_f32"), 2 * N * s, fy, op, p->fN[1], gy);
+    ATKM_RUN(nm<R>("P_y_f64", "P_y_f32", "P_y_df"), 2 * N * s, fy, op, p->fN[1], gy);
   }
   {
     OpPZ<R> op; op.Wk = Wk; op.c = c; op.alpha = alpha_dev;
-    ATKM_RUN(nm<R>("P_z_f64", "P_z_f32"), 2 * N * s, 2.0 * g.Ny * g.Nx * fftflops(g.Nz), op, p->fN[2], gz);
+    ATKM_RUN(nm<R>("P_z_f64", "P_z_f32", "P_z_df"), 2 * N * s, 2.0 * g.Ny * g.Nx * fftflops(g.Nz), op, p->fN[2], gz);
   }
   {
     OpPY<R, 1> op; op.Wk = Wk; op.c = c;
-    ATKM_RUN(nm<R>("P_y_f64", "P_y_f32"), 2 * N * s, fy, op, p->fN[1], gy);
+    ATKM_RUN(nm<R>("P_y_f64", "P_y_f32", "P_y_df"), 2 * N * s, fy, op, p->fN[1], gy);
   }
   {
     OpPXI<R> op; op.Wk = Wk; op.phi = reinterpret_cast<const double2*>(phi); op.Phi = Phi;
     op.Pr = reinterpret_cast<double2*>(Pr); op.c = c; op.ph = pr; op.alpha = alpha_dev;
-    ATKM_RUN(nm<R>("P_x_inv_f64", "P_x_inv_f32"), 40 * N + N * s, fx, op, p->fN[0], gx);
+    ATKM_RUN(nm<R>("P_x_inv_f64", "P_x_inv_f32", "P_x_inv_df"), 40 * N + N * s, fx, op, p->fN[0], gx);
   }
   return cudaSuccess;
 }

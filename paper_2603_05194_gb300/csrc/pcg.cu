@@ -489,11 +489,11 @@ struct PcgBuffers {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // graphs: [f32][parity][kind: 0 iteration, 1 halve+trial, 2 best+trial]
   // captured graphs per [form: FP64, FP32, FP64 with FP32 auxiliaries][parity][kind]
-  cudaGraphExec_t gx[3][2][3] = {};
-  int gnodes[3][2][3] = {};
-  bool seen[3][2][3] = {};
-  bool gprof[3][2][3] = {};                 // captured with profiling events
-  std::vector<ProfRec> grecs[3][2][3];      // those events
+  cudaGraphExec_t gx[4][2][3] = {};
+  int gnodes[4][2][3] = {};
+  bool seen[4][2][3] = {};
+  bool gprof[4][2][3] = {};                 // captured with profiling events
+  std::vector<ProfRec> grecs[4][2][3];      // those events
   const std::vector<ProfRec>* last = nullptr;  // records of the last replay
   bool graphs_ok = true;
   Phys gphys{};
@@ -517,7 +517,7 @@ static void drop_graph(PcgBuffers* b, int f, int q, int k) {
 }
 
 static void destroy_graphs(PcgBuffers* b) {
-  for (int f = 0; f < 3; ++f)
+  for (int f = 0; f < 4; ++f)
     for (int q = 0; q < 2; ++q)
       for (int k = 0; k < 3; ++k) drop_graph(b, f, q, k);
   b->last = nullptr;
@@ -578,6 +578,9 @@ struct Seq {
   // FP64 phase of the split form: the operators that only shape the search
   // direction and the step-size model (P r, H p, the pair ATKM) run in FP32.
   bool aux32 = false;
+  // Double-word form of that phase: H phi and the trial-energy ATKM run in
+  // double-FP32 arithmetic instead of binary64.
+  bool dw = false;
   Ctl* c() const { return B.ctl; }
   const double* s() const { return p->scal; }
   cudaStream_t st() const { return B.st; }
@@ -610,7 +613,8 @@ struct Seq {
   }
   void atkm(int mode, const double* a, const double* b, double* o, bool aux = false) {
     const bool use32 = f32 || (aux && aux32);
-    chk(use32 ? launch_atkm<float>(p, mode, a, b, o, st()) : launch_atkm<double>(p, mode, a, b, o, st()));
+    chk(use32 ? launch_atkm<float>(p, mode, a, b, o, st())
+              : dw ? launch_atkm<df>(p, mode, a, b, o, st()) : launch_atkm<double>(p, mode, a, b, o, st()));
   }
   void hop(const double2* f, double2* o, int red, bool aux = false) {
     const double* fp = reinterpret_cast<const double*>(f);
@@ -618,7 +622,8 @@ struct Seq {
     double* op = reinterpret_cast<double*>(o);
     const bool use32 = f32 || (aux && aux32);
     chk(use32 ? launch_H<float>(p, ph, fp, pp, B.Phi[q], op, red, st())
-              : launch_H<double>(p, ph, fp, pp, B.Phi[q], op, red, st()));
+              : dw ? launch_H<df>(p, ph, fp, pp, B.Phi[q], op, red, st())
+                   : launch_H<double>(p, ph, fp, pp, B.Phi[q], op, red, st()));
   }
   template <typename K, typename... A> void ctl1(K kernel, A... args) {
     kernel<<<1, 1, 0, st()>>>(args...);
@@ -727,7 +732,7 @@ struct Seq {
 static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   PcgBuffers& B = S.B;
   atkm_plan* p = S.p;
-  const int fi = S.f32 ? 1 : (S.aux32 ? 2 : 0);
+  const int fi = S.f32 ? 1 : (S.aux32 ? (S.dw ? 3 : 2) : 0);
   const bool prof = p->prof != nullptr;
   B.last = nullptr;
   if (!use_graphs || !B.graphs_ok) {
@@ -806,7 +811,7 @@ struct Solver {
   PcgBuffers* B = nullptr;
   cudaStream_t caller = nullptr;
   Phys ph{};
-  bool mixed = false, split = false, use_graphs = true, f32 = false, began = false;
+  bool mixed = false, split = false, dwm = false, use_graphs = true, f32 = false, began = false;
   int q = 0, n = 0, n_start = 0, caps = 0, status = ATKM_NOT_CONVERGED, total_h = 0, f32_iters = 0, logc = 0;
   int f32_best_n = 0, early_code = ATKM_OK;
   double linf = INFINITY, f32_best = INFINITY;
@@ -814,13 +819,16 @@ struct Solver {
   atkm_iter_log* L = nullptr;
   cudaError_t err = cudaSuccess;
   const double eps64 = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
+  const double epsdw = 1.4210854715202004e-14;  // 2^-46: double-word operators
+  double eps_polish() const { return dwm ? epsdw : eps64; }
 
   void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
   bool done() const { return st == DONE || err != cudaSuccess; }
   Ctl& H() { return *B->ctl_h; }
   Seq seq(bool is32) {
     Seq S{plan, *B, ph, is32, q};
-    S.aux32 = split && !is32;
+    S.aux32 = (split || dwm) && !is32;
+    S.dw = dwm && !is32;
     return S;
   }
   void fetch_async() { chk(cudaMemcpyAsync(B->ctl_h, B->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, B->st)); }
@@ -837,11 +845,14 @@ struct Solver {
     if (!(opts->tol_residual >= 0.0) || opts->max_iter < 0 || opts->max_halvings < 0)
       return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: bad options");
     split = opts->precision_mode == ATKM_PRECISION_F32_SPLIT;
-    mixed = opts->precision_mode == ATKM_PRECISION_F32_F64 || split;
+    dwm = opts->precision_mode == ATKM_PRECISION_DF32_SPLIT;
+    mixed = opts->precision_mode == ATKM_PRECISION_F32_F64 || split || dwm;
     if (opts->precision_mode != ATKM_PRECISION_F64 && !mixed)
       return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: unknown precision_mode");
     if (mixed && !(plan->flags & ATKM_PLAN_F32))
       return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: mixed precision needs a plan created with ATKM_PLAN_F32");
+    if (dwm && !(plan->flags & ATKM_PLAN_DF32))
+      return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: the double-word form needs a plan created with ATKM_PLAN_DF32");
     logbuf = out->log;
     memset(out, 0, sizeof(*out));
     out->log = logbuf;
@@ -890,7 +901,7 @@ struct Solver {
       fetch_async();
       st = INIT_CHECK;
     }
-    set_scalar(&B->ctl->tolE_eps, 32.0 * (f32 ? eps32 : eps64));
+    set_scalar(&B->ctl->tolE_eps, 32.0 * (f32 ? eps32 : eps_polish()));
     B->valid = false;  // set again when this solve ends cleanly
     return ATKM_OK;
   }
@@ -966,7 +977,7 @@ struct Solver {
           S.atkm(SRC_PSI, reinterpret_cast<const double*>(B->phi[q]), nullptr, B->Phi[q]);
           S.ctl1(k_c_reset_state, B->ctl, 0, 1, 0);
           chk(S.err);
-          set_scalar(&B->ctl->tolE_eps, 32.0 * eps64);
+          set_scalar(&B->ctl->tolE_eps, 32.0 * eps_polish());
           if (L) { --logc; L = nullptr; }
           st = MAIN;
           return;

@@ -107,12 +107,16 @@ struct GLNodes {
 };
 
 // Twiddles e^{-2 pi i m / L}.
-__global__ void k_twiddles(double2* t64, float2* t32, int L) {
+__global__ void k_twiddles(double2* t64, float2* t32, cdf* tdf, int L) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < L; m += gridDim.x * blockDim.x) {
     double s, c;
     sincospi(2.0 * (double)m / (double)L, &s, &c);
     t64[m] = make_double2(c, -s);
     t32[m] = make_float2((float)c, (float)-s);
+    cdf w;
+    w.x = df(c);
+    w.y = df(-s);
+    tdf[m] = w;
   }
 }
 
@@ -201,6 +205,11 @@ __global__ void k_to_f32(float* __restrict__ dst, const double* __restrict__ src
     dst[i] = (float)src[i];
 }
 
+__global__ void k_to_df(df* __restrict__ dst, const double* __restrict__ src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = df(src[i]);
+}
+
 // Fine spectrum <- coarse spectrum / Nc: fine frequency k (signed) takes the
 // coarse coefficient of the same k when -Nc/2 <= k < Nc/2, zero otherwise.
 __global__ void k_embed_spectrum(const double2* __restrict__ coarse, double2* __restrict__ fine, Geo gc, Geo gf,
@@ -243,7 +252,8 @@ bool make_fft_len(int L, FftLen& f) {
 }
 
 void free_plan_memory(atkm_plan* p) {
-  void* ptrs[] = {p->tw64, p->tw32, p->U0, p->U0f, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f, p->partials, p->scal};
+  void* ptrs[] = {p->tw64, p->tw32, p->twdf, p->U0, p->U0f, p->U0d, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f,
+                  p->partials, p->scal};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->scal_host) cudaFreeHost(p->scal_host);
@@ -392,12 +402,14 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   if (!isfinite(nn) || fabs(nn - 1.0) > 1e-12)
     return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: dipole axis must be a unit vector (| |n|-1 | <= 1e-12)");
-  if (flags & ~ATKM_PLAN_F32) return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: unknown flags");
+  if (flags & ~(unsigned)(ATKM_PLAN_F32 | ATKM_PLAN_DF32))
+    return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: unknown flags");
 
   cudaStream_t st = (cudaStream_t)stream;
   atkm_plan* p = new atkm_plan();
   memset(&p->g, 0, sizeof(p->g));
-  p->tw64 = nullptr; p->tw32 = nullptr; p->U0 = nullptr; p->U0f = nullptr; p->W1 = p->W2 = p->T1 = nullptr;
+  p->tw64 = nullptr; p->tw32 = nullptr; p->twdf = nullptr; p->U0 = nullptr; p->U0f = nullptr; p->U0d = nullptr;
+  p->W1 = p->W2 = p->T1 = nullptr;
   p->W1f = p->W2f = p->T1f = nullptr; p->partials = nullptr; p->scal = nullptr; p->scal_host = nullptr;
   p->pcg = nullptr; p->prof = nullptr; p->prof_stopped_ = nullptr; p->bytes = 0; p->flags = flags;
   Geo& g = p->g;
@@ -422,13 +434,15 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   for (int i = 0; i < 6; ++i) twtot += lens[i];
   if ((e = dev_alloc(p, (void**)&p->tw64, twtot * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
   if ((e = dev_alloc(p, (void**)&p->tw32, twtot * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
+  if ((e = dev_alloc(p, (void**)&p->twdf, twtot * sizeof(cdf))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
   size_t off = 0;
   for (int i = 0; i < 6; ++i) {
     FftLen& f = (i < 3) ? p->fN[i] : p->fM[i - 3];
     if (!make_fft_len(lens[i], f)) return bail(fail(nullptr, ATKM_ERR_UNSUPPORTED_SIZE, "plan: FFT factorisation"));
     f.tw64 = p->tw64 + off;
     f.tw32 = p->tw32 + off;
-    k_twiddles<<<(lens[i] + 255) / 256, 256, 0, st>>>(p->tw64 + off, p->tw32 + off, lens[i]);
+    f.twdf = p->twdf + off;
+    k_twiddles<<<(lens[i] + 255) / 256, 256, 0, st>>>(p->tw64 + off, p->tw32 + off, p->twdf + off, lens[i]);
     count_launches(1);
     off += lens[i];
   }
@@ -494,6 +508,11 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
     k_to_f32<<<(int)std::min<size_t>((n_oct + 255) / 256, 4096), 256, 0, st>>>(p->U0f, p->U0, n_oct);
     count_launches(1);
   }
+  if (flags & ATKM_PLAN_DF32) {
+    if ((e = dev_alloc(p, (void**)&p->U0d, n_oct * sizeof(df))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan U0d"));
+    k_to_df<<<(int)std::min<size_t>((n_oct + 255) / 256, 4096), 256, 0, st>>>(p->U0d, p->U0, n_oct);
+    count_launches(1);
+  }
   // reductions: the largest CTA count of a reducing pass, or the vector grid
   long maxb = 1216;
   maxb = std::max<long>(maxb, (long)g.Nz * g.Ny);           // x pass with T = 1
@@ -548,6 +567,14 @@ int dipolar_potential_from_psi_f32(atkm_plan* plan, const double* psi, double* p
   if (!(plan->flags & ATKM_PLAN_F32)) return fail(plan, ATKM_ERR_ARG, "dipolar_potential_from_psi_f32: plan lacks ATKM_PLAN_F32");
   cudaError_t e = launch_atkm<float>(plan, SRC_PSI, psi, nullptr, phi, (cudaStream_t)stream);
   return e == cudaSuccess ? ATKM_OK : cuda_fail(plan, e, "dipolar_potential_from_psi_f32");
+}
+
+int dipolar_potential_from_psi_df32(atkm_plan* plan, const double* psi, double* phi, void* stream) {
+  if (!plan || !psi || !phi) return fail(plan, ATKM_ERR_ARG, "dipolar_potential_from_psi_df32: NULL argument");
+  if (!(plan->flags & ATKM_PLAN_DF32))
+    return fail(plan, ATKM_ERR_ARG, "dipolar_potential_from_psi_df32: plan lacks ATKM_PLAN_DF32");
+  cudaError_t e = launch_atkm<df>(plan, SRC_PSI, psi, nullptr, phi, (cudaStream_t)stream);
+  return e == cudaSuccess ? ATKM_OK : cuda_fail(plan, e, "dipolar_potential_from_psi_df32");
 }
 
 int apply_H(atkm_plan* plan, const atkm_params* prm, const double* f, const double* phi, const double* Phi,

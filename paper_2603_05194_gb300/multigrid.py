@@ -34,7 +34,8 @@ def solve_mg(problem, psi0_fn, levels=3, tol=1e-8, max_iter=20000, precision=B.P
     guess on the coarsest grid.  Returns (per-level results, seconds, finest psi)."""
     grids = level_grids(problem.N, levels)
     f32 = precision != B.PRECISION_F64
-    plans = [B.Plan(N, problem.L, problem.n, f32=f32) for N in grids]
+    df32 = precision == B.PRECISION_DF32_SPLIT
+    plans = [B.Plan(N, problem.L, problem.n, f32=f32, df32=df32) for N in grids]
     try:
         psis = [torch.from_numpy(psi0_fn(problem, grids[0])).cuda()] + \
                [torch.empty(p.shape, dtype=torch.complex128, device="cuda") for p in plans[1:]]
@@ -50,7 +51,8 @@ def solve_mg(problem, psi0_fn, levels=3, tol=1e-8, max_iter=20000, precision=B.P
 
 
 def solve_single(problem, psi0_fn, tol=1e-8, max_iter=20000, precision=B.PRECISION_F32_F64):
-    plan = B.Plan(problem.N, problem.L, problem.n, f32=(precision != B.PRECISION_F64))
+    plan = B.Plan(problem.N, problem.L, problem.n, f32=(precision != B.PRECISION_F64),
+                  df32=(precision == B.PRECISION_DF32_SPLIT))
     try:
         psi = torch.from_numpy(psi0_fn(problem, problem.N)).cuda()
         prm = B.make_params(problem.gamma, problem.beta, problem.lam, problem.Omega)
@@ -77,13 +79,14 @@ def main(argv=None):
     ap.add_argument("--levels", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=20000, help="per level")
-    ap.add_argument("--precision", choices=["split", "mixed", "f64"], default="split")
+    ap.add_argument("--precision", choices=["dwsplit", "split", "mixed", "f64"], default="split")
     ap.add_argument("--single", action="store_true", help="also run the finest grid alone from the same guess")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     B.load_library()
     w = W.CONFIGS[a.workload]
-    prec = {"split": B.PRECISION_F32_SPLIT, "mixed": B.PRECISION_F32_F64, "f64": B.PRECISION_F64}[a.precision]
+    prec = {"dwsplit": B.PRECISION_DF32_SPLIT, "split": B.PRECISION_F32_SPLIT, "mixed": B.PRECISION_F32_F64,
+            "f64": B.PRECISION_F64}[a.precision]
 
     def guess(p, N):
         return W.initial_guess(W.with_grid(p, N))

@@ -115,7 +115,7 @@ def test_apply_H_energy_and_preconditioner_parity(lib, N, L, n):
 
 
 def _run_pair(lib, w, max_iter, tol=1e-8, precision=0):
-    plan = lib.Plan(w.N, w.L, w.n, f32=(precision != 0))
+    plan = lib.Plan(w.N, w.L, w.n, f32=(precision != 0), df32=(precision == 3))
     prm = lib.make_params(w.gamma, w.beta, w.lam, w.Omega)
     psi = dev(W.initial_guess(w))
     res = plan.pcg_ground_state(prm, psi, tol_residual=tol, max_iter=max_iter, log_capacity=max_iter + 2,
@@ -185,10 +185,11 @@ def test_pcg_invariants_along_run(lib):
     assert abs(h3 * float(torch.sum(torch.abs(psi) ** 2)) - 1.0) < 1e-13
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 def test_mixed_precision_reaches_fp64_energy(lib, precision):
-    """FP32 bulk then FP64 polish (1), and the split polish with FP32
-    direction/step-model operators (2): the same FP64 ground state."""
+    """FP32 bulk then FP64 polish (1), the split polish with FP32
+    direction/step-model operators (2), and that polish with H phi and the
+    trial ATKM in double-word arithmetic (3): the same FP64 ground state."""
     w = W.CONFIGS["cfg1_32x32x16"]
     _, _, r64 = _run_pair(lib, w, 400)
     _, _, rmx = _run_pair(lib, w, 400, precision=precision)
@@ -198,7 +199,8 @@ def test_mixed_precision_reaches_fp64_energy(lib, precision):
     assert abs(rmx["mu"] - r64["mu"]) <= 1e-9 * abs(r64["mu"])
 
 
-def test_split_precision_matches_oracle_ground_state(lib):
+@pytest.mark.parametrize("precision", [2, 3])
+def test_split_precision_matches_oracle_ground_state(lib, precision):
     """The split form on a tilted-dipole anisotropic case against the FP64
     oracle's Algorithm 1: E and mu within 1e-10 relative."""
     N, L, n = (24, 20, 12), (5.0, 4.0, 1.2), (0.6, 0.0, 0.8)
@@ -206,13 +208,29 @@ def test_split_precision_matches_oracle_ground_state(lib):
     psi0 = W.guess_phi_d(N, L, gamma, Om)
     ref = O.pcg_ground_state(O.Plan(N, L, n), O.Params(gamma, beta, lam, Om), psi0,
                              O.PcgOptions(tol_residual=1e-9, max_iter=600))
-    plan = lib.Plan(N, L, n, f32=True)
+    plan = lib.Plan(N, L, n, f32=True, df32=(precision == 3))
     psi = dev(psi0)
     r = plan.pcg_ground_state(lib.make_params(gamma, beta, lam, Om), psi, tol_residual=1e-9, max_iter=600,
-                              precision=2)
+                              precision=precision)
     assert ref.status == O.OK and r["status"] == 0
     assert abs(r["E"] - ref.parts["E"]) <= 1e-10 * abs(ref.parts["E"])
     assert abs(r["mu"] - ref.mu) <= 1e-10 * abs(ref.mu)
+
+
+@pytest.mark.parametrize("N,L,n", SMALL_CASES)
+def test_df32_atkm_matches_oracle(lib, N, L, n):
+    """Double-word (double-FP32) ATKM: same 1e-11 bar as the FP64 path; the
+    arithmetic carries about 48 bits (observed 5e-15 - 8e-15 relative)."""
+    plan = lib.Plan(N, L, n, df32=True)
+    oplan = O.Plan(N, L, n)
+    psi = W.random_smooth_field(N, L, (1.0, 1.1, 5.0), seed=103)
+    got = host(plan.dipolar_potential_from_psi(dev(psi), df32=True))
+    assert rel2(got, oplan.dipolar_potential(np.abs(psi) ** 2)) <= 1e-11
+    a = W.random_field((N[2], N[1], N[0]), 104)
+    got = host(plan.dipolar_potential_from_psi(dev(a), df32=True))
+    assert rel2(got, oplan.dipolar_potential(np.abs(a) ** 2)) <= 1e-11
+    with pytest.raises(lib.AtkmError):
+        lib.Plan(N, L, n).dipolar_potential_from_psi(dev(psi), df32=True)
 
 
 def test_f32_atkm_close_to_oracle(lib):
