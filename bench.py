@@ -273,10 +273,11 @@ def rel2(a, b) -> float:
 
 
 def time_to_tol(B, w):
-    """PCG-ATKM-MG (Algorithm 2; levels N/4, N/2, N) in the split precision
-    form from guess (d) on the coarsest grid to residual 1e-8 (computed with
-    FP64 H phi), wall time around the call; plus the FP32-vs-FP64 ATKM error
-    at the final state."""
+    """PCG-ATKM-MG (Algorithm 2; levels N/4, N/2, N) in the double-word split
+    form from guess (d) on the coarsest grid to residual 1e-8 (residual formed
+    from the double-word H phi, about 1e-14 relative), wall time around the
+    call; plus the FP32- and double-word-vs-FP64 ATKM errors at the final
+    state."""
     import torch
     import atkm_workloads as W
     from paper_2603_05194_gb300 import multigrid as MG
@@ -285,22 +286,24 @@ def time_to_tol(B, w):
         return W.initial_guess(W.with_grid(p, N))
 
     res, sec, psi, grids = MG.solve_mg(w, guess, levels=3, tol=TOL, max_iter=20000,
-                                       precision=B.PRECISION_F32_SPLIT)
-    plan = B.Plan(w.N, w.L, w.n, f32=True)
+                                       precision=B.PRECISION_DF32_SPLIT)
+    plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
     try:
         phi64 = plan.dipolar_potential_from_psi(psi)
         phi32 = plan.dipolar_potential_from_psi(psi, f32=True)
+        phidw = plan.dipolar_potential_from_psi(psi, df32=True)
         prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
         e64 = plan.energy_parts(prm, psi, phi64)
         e32 = plan.energy_parts(prm, psi, phi32)
-        err = {"Phi_rel_l2_f32_vs_f64": rel2(phi32, phi64),
+        err = {"Phi_rel_l2_f32_vs_f64": rel2(phi32, phi64), "Phi_rel_l2_df32_vs_f64": rel2(phidw, phi64),
                "E_rel_f32_vs_f64": abs(e32["E"] - e64["E"]) / abs(e64["E"]),
                "mu_rel_f32_vs_f64": abs(e32["mu"] - e64["mu"]) / abs(e64["mu"])}
     finally:
         plan.close()
     out = MG.summary(res, sec, grids)
-    out.update(method="PCG-ATKM-MG, 3 levels, split precision form (FP32 bulk; FP64 polish with H phi, "
-                      "trial-energy ATKM and reductions in FP64, P r / H p / step-model ATKM in FP32)", tol=TOL,
+    out.update(method="PCG-ATKM-MG, 3 levels, double-word split form (FP32 bulk; polish with H phi and the "
+                      "trial-energy ATKM in double-FP32, reductions and retraction in FP64, P r / H p / "
+                      "step-model ATKM in FP32)", tol=TOL,
                precision_errors_at_final_state=err)
     return out
 
@@ -316,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as td
     w = W.CONFIGS[WORKLOAD]
     precision = B.PRECISION_F32_F64 if args.precision == "mixed" else B.PRECISION_F64
-    plan = B.Plan(w.N, w.L, w.n, f32=True)
+    plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
     prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
     psi0_host = torch.from_numpy(W.initial_guess(w)).pin_memory()
     psi0 = psi0_host.cuda()
@@ -346,15 +349,15 @@ def run_ours(args, rank, world, local_rank):
     # ---- stand-alone ATKM evaluations per second (FP64 and FP32 arithmetic)
     Phi = torch.empty(w.shape, dtype=torch.float64, device="cuda")
     standalone = {}
-    for key, f32 in (("f64", False), ("f32", True)):
+    for key, kw in (("f64", {}), ("df32", {"df32": True}), ("f32", {"f32": True})):
         for _ in range(3):
-            plan.dipolar_potential_from_psi(psi0, out=Phi, f32=f32)
+            plan.dipolar_potential_from_psi(psi0, out=Phi, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         n = 50
         e0.record()
         for _ in range(n):
-            plan.dipolar_potential_from_psi(psi0, out=Phi, f32=f32)
+            plan.dipolar_potential_from_psi(psi0, out=Phi, **kw)
         e1.record()
         torch.cuda.synchronize()
         standalone[key] = round(n / (e0.elapsed_time(e1) * 1e-3), 1)
