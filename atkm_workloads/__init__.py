@@ -238,3 +238,31 @@ def guess_draws(count: int, seed: int = 5, N=GUESS_COARSE_N):
 def with_grid(w: Workload, N) -> Workload:
     """The same problem on another grid of the same box."""
     return Workload(w.name, tuple(N), w.L, w.gamma, w.beta, w.lam, w.n, w.Omega, w.guess, w.seed, dict(w.extra))
+
+
+PAPER_GUESS_NAMES = ("a", "b", "bbar", "c", "cbar", "d", "dbar", "e", "ebar", "f")
+
+
+def paper_guesses(N, L, gamma, beta, Omega) -> dict:
+    """The ten initial guesses of §3, each normalised in the discrete norm:
+    (a) the unit-width Gaussian exp(-|x|^2/2); (b) (x + i y) times it; (c) a + b;
+    (d) (1 - Omega) a + Omega b; (e) Omega a + (1 - Omega) b, each of b-e with
+    its complex conjugate; (f) the Thomas-Fermi profile sqrt(max(mu_TF - V, 0)/beta)
+    with mu_TF = (1/2) (15 beta gamma_x gamma_y gamma_z / (4 pi))^(2/5)."""
+    x, y, z = mesh(N, L)
+    shape = (N[2], N[1], N[0])
+
+    def nrm(f):
+        f = np.broadcast_to(f, shape).astype(np.complex128)
+        return f / _l2(f, N, L)
+
+    pa = nrm(np.exp(-(x * x + y * y + z * z) / 2))
+    pb = nrm((x + 1j * y) * pa)
+    V = 0.5 * (gamma[0] * x * x + gamma[1] * y * y + gamma[2] * z * z)
+    mu_tf = 0.5 * (15.0 * beta * gamma[0] * gamma[1] * gamma[2] / (4.0 * math.pi)) ** 0.4
+    g = {"a": pa, "b": pb, "c": nrm(pa + pb), "d": nrm((1 - Omega) * pa + Omega * pb),
+         "e": nrm(Omega * pa + (1 - Omega) * pb)}
+    for k in ("b", "c", "d", "e"):
+        g[k + "bar"] = np.conj(g[k])
+    g["f"] = nrm(np.sqrt(np.maximum(mu_tf - V, 0.0) / beta))
+    return {k: g[k] for k in PAPER_GUESS_NAMES}
