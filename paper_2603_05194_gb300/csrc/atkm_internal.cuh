@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/atkm.h"
@@ -71,16 +72,27 @@ template <> __device__ __forceinline__ df tor<df>(double v) {
 }
 template <> __device__ __forceinline__ double tod<df>(df v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
 
-template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
-template <typename R> __device__ __forceinline__ cx<R> sub(cx<R> a, cx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
-template <typename R> __device__ __forceinline__ cx<R> scl(cx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) {
+  if constexpr (std::is_same<R, df>::value) return df_cadd(a, b);
+  else return mk<R>(a.x + b.x, a.y + b.y);
+}
+template <typename R> __device__ __forceinline__ cx<R> sub(cx<R> a, cx<R> b) {
+  if constexpr (std::is_same<R, df>::value) return df_csub(a, b);
+  else return mk<R>(a.x - b.x, a.y - b.y);
+}
+template <typename R> __device__ __forceinline__ cx<R> scl(cx<R> a, R s) {
+  if constexpr (std::is_same<R, df>::value) return df_cscl(a, s);
+  else return mk<R>(a.x * s, a.y * s);
+}
 // a * b
 template <typename R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
-  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  if constexpr (std::is_same<R, df>::value) return df_cmul(a, b, false);
+  else return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 // a * conj(b)
 template <typename R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
-  return mk<R>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+  if constexpr (std::is_same<R, df>::value) return df_cmul(a, b, true);
+  else return mk<R>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 // s * i * a  (s = +1 or -1)
 template <typename R, int S> __device__ __forceinline__ cx<R> mul_si(cx<R> a) {

@@ -47,14 +47,14 @@ __device__ __forceinline__ df df_fast_two_sum(float a, float b) {
   return df(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
-static __device__ __noinline__ df operator+(df a, df b) {
+__device__ __forceinline__ df operator+(df a, df b) {
   const df s = df_two_sum(a.hi, b.hi);
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 __device__ __forceinline__ df& operator+=(df& a, df b) { a = a + b; return a; }
-static __device__ __noinline__ df operator*(df a, df b) {
+__device__ __forceinline__ df operator*(df a, df b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the leading product
   e = __fmaf_rn(a.hi, b.lo, e);
@@ -77,6 +77,37 @@ __device__ __forceinline__ df df_rsqrt(df v) {
   const df y(rsqrtf(v.hi), 0.0f);
   const df e = df(1.0f, 0.0f) - v * (y * y);
   return y + y * (df(0.5f, 0.0f) * e);
+}
+
+// Complex operations are out-of-line functions: every butterfly and twiddle
+// of the FFT engine calls them, so each double-word kernel contains one copy
+// of their code instead of one per call site (a fully inlined instantiation
+// of the ATKM passes took minutes of nvcc time), at the price of a call.
+static __device__ __noinline__ cdf df_cadd(cdf a, cdf b) {
+  cdf r;
+  r.x = a.x + b.x;
+  r.y = a.y + b.y;
+  return r;
+}
+static __device__ __noinline__ cdf df_csub(cdf a, cdf b) {
+  cdf r;
+  r.x = a.x - b.x;
+  r.y = a.y - b.y;
+  return r;
+}
+// a * b (conj_b = false) or a * conj(b) (conj_b = true)
+static __device__ __noinline__ cdf df_cmul(cdf a, cdf b, bool conj_b) {
+  const df by = conj_b ? -b.y : b.y;
+  cdf r;
+  r.x = a.x * b.x - a.y * by;
+  r.y = a.x * by + a.y * b.x;
+  return r;
+}
+static __device__ __noinline__ cdf df_cscl(cdf a, df s) {
+  cdf r;
+  r.x = a.x * s;
+  r.y = a.y * s;
+  return r;
 }
 
 }  // namespace atkm
