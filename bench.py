@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-precision-form", action="store_true", help="skip the FP32-bulk arm")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solve to 1e-8")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "pcg_f64", "pcg_mixed"],
+    ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture and exit")
     return ap.parse_args()
 
@@ -401,11 +401,11 @@ def profile_case(case: str):
     import atkm_workloads as W
     from paper_2603_05194_gb300 import binding as B
     w = W.CONFIGS[WORKLOAD]
-    plan = B.Plan(w.N, w.L, w.n, f32=True)
+    plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
     psi = torch.from_numpy(W.initial_guess(w)).cuda()
     if case.startswith("atkm"):
         for _ in range(2):
-            Phi = plan.dipolar_potential_from_psi(psi, f32=(case == "atkm_f32"))
+            Phi = plan.dipolar_potential_from_psi(psi, f32=(case == "atkm_f32"), df32=(case == "atkm_df32"))
         torch.cuda.synchronize()
         print(case, "max|Phi|", float(Phi.abs().max()))
     else:
