@@ -29,7 +29,7 @@ def _timed(fn):
 
 def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PRECISION_F32_F64, B.PRECISION_F64),
         log=print):
-    plans = [B.Plan(p.N, p.L, p.n, f32=True) for p in problems]
+    plans = [B.Plan(p.N, p.L, p.n, f32=True, df32=True) for p in problems]
     prms = [B.make_params(p.gamma, p.beta, p.lam, p.Omega) for p in problems]
 
     def psis():
@@ -55,12 +55,12 @@ def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PR
         if full_iters > 0:
             ps = psis()
             res, t = _timed(lambda: B.pcg_ground_state_batched(plans, prms, ps, max_iter=full_iters, tol_residual=tol,
-                                                               precision=B.PRECISION_F32_F64))
+                                                               precision=B.PRECISION_DF32_SPLIT))
             st = collections.Counter(r["status_name"] for r in res)
             out["full"] = dict(tol=tol, max_iter=full_iters, seconds=t, statuses=dict(st),
                                iters=[r["iters"] for r in res], residual=[r["residual"] for r in res],
                                E=[r["E"] for r in res])
-            log(f"sweep to {tol:g} (mixed, at most {full_iters} iterations): {t:.1f} s, {dict(st)}")
+            log(f"sweep to {tol:g} (double-word split form, at most {full_iters} iterations): {t:.1f} s, {dict(st)}")
     finally:
         for pl in plans:
             pl.close()
