@@ -15,6 +15,7 @@
 
 #include <math.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "atkm_internal.cuh"
@@ -313,15 +314,27 @@ template <typename K> inline cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Dynamic shared memory above the default must be opted into once per kernel
+// and device (the attribute belongs to the device's context); `done` holds
+// one bit per device already prepared.
+template <typename K>
+inline cudaError_t ensure_smem(std::atomic<unsigned long long>& done, K kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = set_smem(kernel, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 template <typename R, int L, class Op>
 inline cudaError_t launch_fast_L(const Op& op, const FftLen& f, const PassGrid& pg, cudaStream_t st) {
-  static bool prepared = false;
+  static std::atomic<unsigned long long> prepared{0};
   const size_t sm = FastSmem<R, L>::bytes;
-  if (!prepared) {
-    cudaError_t e = set_smem(k_fast<R, L, Op>, sm);
-    if (e != cudaSuccess) return e;
-    prepared = true;
-  }
+  cudaError_t e = ensure_smem(prepared, k_fast<R, L, Op>, sm);
+  if (e != cudaSuccess) return e;
   k_fast<R, L, Op><<<pg.grid, kThreads, sm, st>>>(op, tw_table_host<R>(f));
   return cudaGetLastError();
 }
@@ -339,12 +352,9 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
       default: return launch_fast_L<R, 1024>(op, f, pg, st);
     }
   }
-  static bool prepared = false;
-  if (!prepared) {
-    cudaError_t e = set_smem(k_generic<R, Op>, (size_t)(TileElems<R>::value + kMaxLen) * sizeof(cx<R>));
-    if (e != cudaSuccess) return e;
-    prepared = true;
-  }
+  static std::atomic<unsigned long long> prepared{0};
+  cudaError_t e = ensure_smem(prepared, k_generic<R, Op>, (size_t)(TileElems<R>::value + kMaxLen) * sizeof(cx<R>));
+  if (e != cudaSuccess) return e;
   const size_t sm = (size_t)(pg.T * f.L + f.L) * sizeof(cx<R>);
   k_generic<R, Op><<<pg.grid, kThreads, sm, st>>>(op, f, pg.T);
   return cudaGetLastError();
