@@ -125,7 +125,17 @@ struct FftLen {
   const double2* tw64;  // e^{-2 pi i m / L}, m = 0..L-1
   const float2* tw32;
   const cdf* twdf;      // the binary64 table split into double-word
+  const double2* lf64;  // tw64 in multiply-add form (m, t), see lf_cform
 };
+
+// Multiply-add form of the twiddle W_j = e^{-2 pi i j / L} = c + i s: with
+// |t| <= 1, W_j = m (1 + i t) (m = c, t = s / c) when |c| >= |s| (the
+// "c-form"), else W_j = m (t + i) (m = s, t = c / s).  The form follows from j
+// alone: |c| >= |s| exactly when q = j mod L/2 lies in [0, L/8] or [3L/8, L/2).
+__host__ __device__ __forceinline__ bool lf_cform(int j, int L) {
+  const int q = j % (L >> 1);
+  return 8 * q <= L || 8 * q >= 3 * L;
+}
 
 template <typename R> __host__ __device__ __forceinline__ const cx<R>* tw_table(const FftLen& f);
 template <> __host__ __device__ __forceinline__ const double2* tw_table<double>(const FftLen& f) { return f.tw64; }
@@ -144,11 +154,16 @@ template <typename R> inline const cx<R>* tw_table_host(const FftLen& f) { retur
 // In-register R-point DFT, X_q = sum_r v_r e^{S 2 pi i r q / R}.
 template <typename R, int RAD, int S> struct Dft;
 
+// run: the full DFT.  run_zu: inputs in the upper half are zero (the zero
+// padding of a forward transform) and are not read.  run_lo: only outputs in
+// the lower half are formed (the crop after an inverse transform); the others
+// are left unspecified.
 template <typename R, int S> struct Dft<R, 2, S> {
   static __device__ __forceinline__ void run(cx<R>* v) {
     cx<R> a = v[0], b = v[1];
     v[0] = add<R>(a, b); v[1] = sub<R>(a, b);
   }
+  static __device__ __forceinline__ void run_lo(cx<R>* v) { v[0] = add<R>(v[0], v[1]); }
 };
 template <typename R, int S> struct Dft<R, 4, S> {
   static __device__ __forceinline__ void run(cx<R>* v) {
@@ -157,23 +172,48 @@ template <typename R, int S> struct Dft<R, 4, S> {
     v[0] = add<R>(a, c); v[2] = sub<R>(a, c);
     v[1] = add<R>(b, d); v[3] = sub<R>(b, d);
   }
+  static __device__ __forceinline__ void run_zu(cx<R>* v) {  // v[2] = v[3] = 0
+    const cx<R> a = v[0], c = v[1], d = mul_si<R, S>(v[1]);
+    v[0] = add<R>(a, c); v[2] = sub<R>(a, c);
+    v[1] = add<R>(a, d); v[3] = sub<R>(a, d);
+  }
+  static __device__ __forceinline__ void run_lo(cx<R>* v) {  // v[0], v[1] only
+    cx<R> a = add<R>(v[0], v[2]), b = sub<R>(v[0], v[2]);
+    cx<R> c = add<R>(v[1], v[3]), d = mul_si<R, S>(sub<R>(v[1], v[3]));
+    v[0] = add<R>(a, c); v[1] = add<R>(b, d);
+  }
 };
 template <typename R, int S> struct Dft<R, 8, S> {
-  static __device__ __forceinline__ void run(cx<R>* v) {
+  template <bool ZU, bool LO>
+  static __device__ __forceinline__ void go(cx<R>* v) {
     cx<R> e[4] = {v[0], v[2], v[4], v[6]};
     cx<R> o[4] = {v[1], v[3], v[5], v[7]};
-    Dft<R, 4, S>::run(e);
-    Dft<R, 4, S>::run(o);
+    if (ZU) {
+      Dft<R, 4, S>::run_zu(e);
+      Dft<R, 4, S>::run_zu(o);
+    } else {
+      Dft<R, 4, S>::run(e);
+      Dft<R, 4, S>::run(o);
+    }
     const R c = (R)ATKM_SQRT1_2;
     // o_q *= e^{S i pi q / 4}
     cx<R> o1 = mk<R>(c * (o[1].x - S * o[1].y), c * (o[1].y + S * o[1].x));
     cx<R> o2 = mul_si<R, S>(o[2]);
     cx<R> o3 = mk<R>(-c * (o[3].x + S * o[3].y), c * (S * o[3].x - o[3].y));
-    v[0] = add<R>(e[0], o[0]); v[4] = sub<R>(e[0], o[0]);
-    v[1] = add<R>(e[1], o1);   v[5] = sub<R>(e[1], o1);
-    v[2] = add<R>(e[2], o2);   v[6] = sub<R>(e[2], o2);
-    v[3] = add<R>(e[3], o3);   v[7] = sub<R>(e[3], o3);
+    v[0] = add<R>(e[0], o[0]);
+    v[1] = add<R>(e[1], o1);
+    v[2] = add<R>(e[2], o2);
+    v[3] = add<R>(e[3], o3);
+    if (!LO) {
+      v[4] = sub<R>(e[0], o[0]);
+      v[5] = sub<R>(e[1], o1);
+      v[6] = sub<R>(e[2], o2);
+      v[7] = sub<R>(e[3], o3);
+    }
   }
+  static __device__ __forceinline__ void run(cx<R>* v) { go<false, false>(v); }
+  static __device__ __forceinline__ void run_zu(cx<R>* v) { go<true, false>(v); }
+  static __device__ __forceinline__ void run_lo(cx<R>* v) { go<false, true>(v); }
 };
 template <typename R, int S> struct Dft<R, 3, S> {
   static __device__ __forceinline__ void run(cx<R>* v) {
@@ -353,9 +393,11 @@ struct atkm_plan {
   atkm::FftLen fM[3];  // padded lengths 2N_x, 2N_y, 2N_z
   double2* tw64;       // twiddle pool
   float2* tw32;
+  double2* lf64;       // binary64 twiddles in multiply-add form
   double* U0;          // octant (Nz+1)(Ny+1)(Nx+1)
   float* U0f;          // FP32 copy of U0 (FP32 workspaces only)
-  atkm::df* U0d;       // double-word copy of U0 (ATKM_PLAN_DF32 only)
+  double* Kz;          // z-pass multiplier K_sym / (Mx My Mz), [Mz][My][XS] half spectrum
+  atkm::df* Kzd;       // double-word copy of Kz (ATKM_PLAN_DF32 only)
   atkm::cdf* twdf;     // double-word twiddle pool
   double2* W1;         // [Nz][Ny][XS] half spectrum in x
   double2* W2;         // [Nz][My][XS]

@@ -86,25 +86,115 @@ template <typename R, int L, bool LM> __device__ __forceinline__ int fsa(int t, 
   return lin + (lin >> SmemShift<R>::value);
 }
 
+// ---- binary64 twiddled butterflies in multiply-add form (Linzer and Feig's
+// modified FFT butterflies).  W = e^{S 2 pi i j / L} is read as (m, t) from
+// the multiply-add table of e^{-2 pi i j / L} (conjugated for S > 0), so that
+// W x = m y with y one FMA a component, and a +/- W x one FMA more a component:
+// 6 FP64 instructions a butterfly instead of 8 (complex product, then add and
+// subtract).  The form (lf_cform) is an integer test on j.  Nothing on the
+// FP64 pipe depends on it: it swaps operands with selects and flips the sign
+// of a scale factor with an integer XOR, and the remaining signs are the same
+// for every thread and fold into the FMAs.
+
+// a with its sign flipped when f (an integer operation on the high word).
+__device__ __forceinline__ double flip_sign(double a, bool f) {
+  return __hiloint2double(__double2hiint(a) ^ (f ? (int)0x80000000 : 0), __double2loint(a));
+}
+
+template <int L, int S, bool LO>
+__device__ __forceinline__ void lf_bfly(double2& a, double2& x, const double2* lf, int j) {
+  const double2 e = lf[j];
+  const bool sf = !lf_cform(j, L);
+  // W = m_e (1 + i t_e) or m_e (t_e + i): t_e = t and m_e = m for S < 0; for
+  // S > 0 (conjugate) t_e = -t, and m_e = -m in the s-form
+  const double t = (S > 0) ? -e.y : e.y;
+  const double mi = (S > 0) ? flip_sign(e.x, sf) : e.x;
+  const double mr = flip_sign(mi, sf);
+  // (P, Q) = (x.x, x.y) in the c-form, swapped in the s-form; then
+  // W x = (mr u, mi v) with u = P - t_e Q, v = Q + t_e P in both forms
+  const double P = sf ? x.y : x.x, Q = sf ? x.x : x.y;
+  const double u = fma(-t, Q, P), v = fma(t, P, Q);
+  if (!LO) x = make_double2(fma(-mr, u, a.x), fma(-mi, v, a.y));  // a - W x
+  a = make_double2(fma(mr, u, a.x), fma(mi, v, a.y));               // a + W x
+}
+
+// Twiddled radix-8 step: v[r] <- W^r v[r] (W = W_j), then the DFT of sign S,
+// as three layers of four multiply-add butterflies.  With r = 4 b2 + 2 b1 + b0
+// the layers apply W^4; W^2 and S i W^2 (= W_{2j + L/4}); and W, theta W,
+// theta^2 W, theta^3 W (theta = e^{S i pi / 4}, W_{j + qL/8}), where each odd
+// partial sum carries the common factor of its inputs so that one table
+// twiddle a butterfly suffices.  LO: only X_0..X_3 are formed.
+template <int L, int S, bool LO>
+__device__ __forceinline__ void lf_radix8(double2 (&v)[8], const double2* lf, int j) {
+  constexpr int L8 = L / 8, L4 = L / 4;
+  // v0 +/- W^4 v4, v2 +/- W^4 v6, v1 +/- W^4 v5, v3 +/- W^4 v7
+  lf_bfly<L, S, false>(v[0], v[4], lf, 4 * j);
+  lf_bfly<L, S, false>(v[2], v[6], lf, 4 * j);
+  lf_bfly<L, S, false>(v[1], v[5], lf, 4 * j);
+  lf_bfly<L, S, false>(v[3], v[7], lf, 4 * j);
+  // evens: E0, E2 in v0, v2; E1, E3 in v4, v6.  Odds / W: in v1, v3 and v5, v7
+  lf_bfly<L, S, false>(v[0], v[2], lf, 2 * j);
+  lf_bfly<L, S, false>(v[4], v[6], lf, 2 * j + L4);
+  lf_bfly<L, S, false>(v[1], v[3], lf, 2 * j);
+  lf_bfly<L, S, false>(v[5], v[7], lf, 2 * j + L4);
+  // X_q = E_q + theta^q O_q, X_{q+4} = E_q - theta^q O_q
+  lf_bfly<L, S, LO>(v[0], v[1], lf, j);           // X0, X4
+  lf_bfly<L, S, LO>(v[4], v[5], lf, j + L8);      // X1, X5
+  lf_bfly<L, S, LO>(v[2], v[3], lf, j + L4);      // X2, X6
+  lf_bfly<L, S, LO>(v[6], v[7], lf, j + 3 * L8);  // X3, X7
+  const double2 x1 = v[4], x3 = v[6], x4 = v[1], x6 = v[3];
+  v[1] = x1; v[3] = x3; v[4] = x4; v[6] = x6;
+}
+
+// Twiddled radix-4 step (W = W_b): v[q] <- W^q v[q], then the DFT of sign S:
+// v0 +/- W^2 v2, v1 +/- W^2 v3, then W and S i W (= W_{b + L/4}).  LO: only
+// X_0, X_1 are formed.
+template <int L, int S, bool LO>
+__device__ __forceinline__ void lf_radix4(double2 (&u)[4], const double2* lf, int b) {
+  lf_bfly<L, S, false>(u[0], u[2], lf, 2 * b);
+  lf_bfly<L, S, false>(u[1], u[3], lf, 2 * b);
+  lf_bfly<L, S, LO>(u[0], u[1], lf, b);           // X0, X2
+  lf_bfly<L, S, LO>(u[2], u[3], lf, b + L / 4);   // X1, X3
+  const double2 x1 = u[2], x2 = u[1];
+  u[1] = x1; u[2] = x2;
+}
+
 // Transforms the 8 register elements v[r] = line[j + TPL r] of line t in place
-// (sign S, unnormalised); on return v[r] holds frequency j + TPL r.
-template <typename R, int L, int S, bool LM>
+// (sign S, unnormalised); on return v[r] holds frequency j + TPL r.  ZU: the
+// elements r >= 4 (positions >= L/2) are zero and not read.  LO: only the
+// outputs r < 4 (frequencies < L/2) are formed.
+template <typename R, int L, int S, bool LM, bool ZU = false, bool LO = false>
 __device__ __forceinline__ void fast_fft(cx<R> (&v)[8], cx<R>* b0, cx<R>* b1, const cx<R>* tw, int t, int j) {
   using C = FastCfg<L>;
+  static_assert(!(ZU && LO && C::A == 1 && C::REM == 1), "ZU and LO in one radix-8 stage");
+  constexpr bool kLF = std::is_same<R, double>::value;  // tw is the multiply-add table
   int Ns = 1;
 #pragma unroll
   for (int s = 0; s < C::A; ++s) {
     const int k = j & (Ns - 1);
-    if (s > 0) {
-      const int tws = L / (8 * Ns);
-#pragma unroll
-      for (int r = 1; r < 8; ++r) {
-        const cx<R> w = tw[k * r * tws];
-        v[r] = (S < 0) ? cmul<R>(v[r], w) : cmulc<R>(v[r], w);
-      }
-    }
-    Dft<R, 8, S>::run(v);
     const bool last = (s == C::A - 1) && (C::REM == 1);
+    if constexpr (kLF) {
+      if (s == 0) {
+        if (ZU) Dft<R, 8, S>::run_zu(v);
+        else Dft<R, 8, S>::run(v);
+      } else if (LO && last) {
+        lf_radix8<L, S, true>(v, tw, k * (L / (8 * Ns)));
+      } else {
+        lf_radix8<L, S, false>(v, tw, k * (L / (8 * Ns)));
+      }
+    } else {
+      if (s > 0) {
+        const int tws = L / (8 * Ns);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) {
+          const cx<R> w = tw[k * r * tws];
+          v[r] = (S < 0) ? cmul<R>(v[r], w) : cmulc<R>(v[r], w);
+        }
+      }
+      if (ZU && s == 0) Dft<R, 8, S>::run_zu(v);
+      else if (LO && last) Dft<R, 8, S>::run_lo(v);
+      else Dft<R, 8, S>::run(v);
+    }
     if (!last) {
       cx<R>* b = (s & 1) ? b1 : b0;
       const int base = (j - k) * 8 + k;
@@ -124,14 +214,21 @@ __device__ __forceinline__ void fast_fft(cx<R> (&v)[8], cx<R>* b0, cx<R>* b1, co
       cx<R> u[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) u[q] = v[m + M * q];
+      if constexpr (kLF && Q == 2) {
+        lf_bfly<L, S, LO>(u[0], u[1], tw, b);
+      } else if constexpr (kLF && Q == 4) {
+        lf_radix4<L, S, LO>(u, tw, b);
+      } else {
 #pragma unroll
-      for (int q = 1; q < Q; ++q) {
-        const cx<R> w = tw[b * q];
-        u[q] = (S < 0) ? cmul<R>(u[q], w) : cmulc<R>(u[q], w);
+        for (int q = 1; q < Q; ++q) {
+          const cx<R> w = tw[b * q];
+          u[q] = (S < 0) ? cmul<R>(u[q], w) : cmulc<R>(u[q], w);
+        }
+        if (LO) Dft<R, Q, S>::run_lo(u);
+        else Dft<R, Q, S>::run(u);
       }
-      Dft<R, Q, S>::run(u);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) v[m + M * q] = u[q];
+      for (int q = 0; q < (LO ? Q / 2 : Q); ++q) v[m + M * q] = u[q];
     }
   }
 }
@@ -143,6 +240,8 @@ template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
   static constexpr int kRed = NRED;        // fused reduction slots
   static constexpr bool kLM = LM;          // line-major (x) pass
   static constexpr bool kMirror = false;   // post-processing needs the mirror frequency L - k
+  static constexpr bool kZeroUpper = false;  // positions >= L/2 of the first transform's input are zero
+  static constexpr bool kHalfOut = false;    // only positions < L/2 of the last transform's output are used
   double* part = nullptr;                  // reduction partials [slot][block]
   int pstride = 0;
 };
@@ -177,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : (std::is_same<R
   const bool ok = op.valid(o, x);
   cx<R> v[8];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = ok ? op.load(o, x, j + C::TPL * r) : czero<R>();
+  for (int r = 0; r < 8; ++r) v[r] = (ok && (!Op::kZeroUpper || r < 4)) ? op.load(o, x, j + C::TPL * r) : czero<R>();
   // FP64 twiddles are staged in shared memory; FP32 twiddles are read through
   // L1 from global memory, which avoids the bank conflicts of the strided
   // table accesses (the FP32 passes are issue-bound, the FP64 ones ALU-bound).
@@ -191,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : (std::is_same<R
   R acc[NR];
 #pragma unroll
   for (int s = 0; s < NR; ++s) acc[s] = (R)0;
-  fast_fft<R, L, Op::kSign1, Op::kLM>(v, b0, b1, twsrc, t, j);
+  constexpr bool kLo1 = Op::kHalfOut && !Op::kSecond && !Op::kMirror;
+  fast_fft<R, L, Op::kSign1, Op::kLM, Op::kZeroUpper, kLo1>(v, b0, b1, twsrc, t, j);
   if constexpr (Op::kMirror) {
     // exchange so every thread sees the frequency L - k of each of its k
     __syncthreads();
@@ -212,11 +312,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : (std::is_same<R
     }
     if (Op::kSecond) {
       __syncthreads();
-      fast_fft<R, L, -Op::kSign1, Op::kLM>(v, b0, b1, twsrc, t, j);
+      fast_fft<R, L, -Op::kSign1, Op::kLM, false, Op::kHalfOut>(v, b0, b1, twsrc, t, j);
     }
     if (ok) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
+      for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
     }
   }
   if (Op::kRed > 0) reduce_out<R, NR>(acc, op.part, op.pstride);
@@ -335,7 +435,9 @@ inline cudaError_t launch_fast_L(const Op& op, const FftLen& f, const PassGrid& 
   const size_t sm = FastSmem<R, L>::bytes;
   cudaError_t e = ensure_smem(prepared, k_fast<R, L, Op>, sm);
   if (e != cudaSuccess) return e;
-  k_fast<R, L, Op><<<pg.grid, kThreads, sm, st>>>(op, tw_table_host<R>(f));
+  // binary64 passes take the multiply-add form of the twiddles
+  const cx<R>* tw = std::is_same<R, double>::value ? reinterpret_cast<const cx<R>*>(f.lf64) : tw_table_host<R>(f);
+  k_fast<R, L, Op><<<pg.grid, kThreads, sm, st>>>(op, tw);
   return cudaGetLastError();
 }
 
@@ -373,6 +475,7 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
 // W1: [Nz][Ny][XS], W2: [Nz][My][XS], columns 0..Nx used.
 template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
   static constexpr bool kMirror = true;
+  static constexpr bool kZeroUpper = true;  // z_m = 0 for m >= Nx/2 = L/2
   const double* a; const double* b; cx<R>* W1; const cx<R>* twM; Cst<R> c; int XS;
   __device__ R dens(size_t idx) const {
     if (MODE == SRC_RHO) return tor<R>(a[idx]);
@@ -406,6 +509,7 @@ template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
 
 // y forward: o = z, x = kx in [0, Nx]; rows y < Ny of W1, zero beyond.
 template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
+  static constexpr bool kZeroUpper = true;  // rows y >= Ny = L/2 are the padding
   const cx<R>* W1; cx<R>* W2; Cst<R> c; int XS;
   __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const {
@@ -418,22 +522,34 @@ template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
 // z forward * K_sym / (Mx My Mz) * inverse: o = ky, x = kx in [0, Nx]; rows z < Nz.
 // K_sym = (K(k) + K(-k))/2 = -1 + 3 U0 (A^2 + B^2), A = sum of n_a nu_a over
 // axes whose index is not the padded Nyquist index, B over those that are.
+// FP64 and double-word passes are bound by arithmetic: they read K_sym, pre-
+// scaled, from the plan's table in the layout of W2 (k_multiplier_half; 8 B a
+// point, about 9 FP64 instructions fewer).  FP32 passes are bound by issue and
+// bandwidth: they form it from the U0 octant (mostly L2-resident), which
+// costs less than the table's extra 4 B a point.
 template <typename R> struct OpAtkmZ : OpBase<-1, true, 0, false> {
-  cx<R>* W2; const R* U0; Cst<R> c; R n0, n1, n2, invM; int XS;
+  static constexpr bool kZeroUpper = true;  // rows z >= Nz = L/2 are the padding
+  static constexpr bool kHalfOut = true;    // only rows z < Nz are kept
+  static constexpr bool kTable = !std::is_same<R, float>::value;
+  cx<R>* W2; const R* K; const R* U0; Cst<R> c; R n0, n1, n2, invM; int XS;
   __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const {
     return pos < c.Nz ? W2[((size_t)pos * c.My + o) * XS + x] : czero<R>();
   }
   __device__ void spectral(int o, int x, int k, cx<R>& v, R*) const {
-    const int ky = kfreq(o, c.My), kz = kfreq(k, c.Mz);
-    const int kx = x == c.Nx ? -c.Nx : x;  // signed frequency of the half-spectrum column
-    const R tx = n0 * ((R)kx * c.pkx), ty = n1 * ((R)ky * c.pky), tz = n2 * ((R)kz * c.pkz);
-    R A = (R)0, B = (R)0;
-    if (x == c.Nx) B += tx; else A += tx;
-    if (o == c.Ny) B += ty; else A += ty;
-    if (k == c.Nz) B += tz; else A += tz;
-    const R u = U0[((size_t)iabs(kz) * (c.Ny + 1) + iabs(ky)) * (c.Nx + 1) + x];
-    v = scl<R>(v, ((R)3 * u * (A * A + B * B) - (R)1) * invM);
+    if constexpr (kTable) {
+      v = scl<R>(v, K[((size_t)k * c.My + o) * XS + x]);
+    } else {
+      const int ky = kfreq(o, c.My), kz = kfreq(k, c.Mz);
+      const int kx = x == c.Nx ? -c.Nx : x;  // signed frequency of the half-spectrum column
+      const R tx = n0 * ((R)kx * c.pkx), ty = n1 * ((R)ky * c.pky), tz = n2 * ((R)kz * c.pkz);
+      R A = (R)0, B = (R)0;
+      if (x == c.Nx) B += tx; else A += tx;
+      if (o == c.Ny) B += ty; else A += ty;
+      if (k == c.Nz) B += tz; else A += tz;
+      const R u = U0[((size_t)iabs(kz) * (c.Ny + 1) + iabs(ky)) * (c.Nx + 1) + x];
+      v = scl<R>(v, ((R)3 * u * (A * A + B * B) - (R)1) * invM);
+    }
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R*) const {
     if (pos < c.Nz) W2[((size_t)pos * c.My + o) * XS + x] = v;
@@ -442,6 +558,7 @@ template <typename R> struct OpAtkmZ : OpBase<-1, true, 0, false> {
 
 // y inverse: o = z, x = kx in [0, Nx]; output rows y < Ny into W1.
 template <typename R> struct OpAtkmYI : OpBase<1, false, 0, false> {
+  static constexpr bool kHalfOut = true;  // only rows y < Ny = L/2 are kept
   const cx<R>* W2; cx<R>* W1; Cst<R> c; int XS;
   __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const { return W2[((size_t)o * c.My + pos) * XS + x]; }
@@ -455,6 +572,7 @@ template <typename R> struct OpAtkmYI : OpBase<1, false, 0, false> {
 // (X_k - conj X_{Nx-k}), k < Nx, then an inverse FFT of length Nx gives
 // z_m = Phi_{2m} + i Phi_{2m+1}; kept for 2m < Nx (the crop).
 template <typename R> struct OpAtkmXI : OpBase<1, false, 0, true> {
+  static constexpr bool kHalfOut = true;  // only z_m with 2m < Nx, i.e. m < L/2, are kept
   const cx<R>* W1; double* phi; const cx<R>* twM; Cst<R> c; int XS;
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
   __device__ cx<R> load(int o, int, int k) const {

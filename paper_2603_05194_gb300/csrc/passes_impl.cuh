@@ -21,10 +21,12 @@ template <typename R> inline cx<R>* ws3(atkm_plan* p);
 template <> inline double2* ws3<double>(atkm_plan* p) { return p->T1; }
 template <> inline float2* ws3<float>(atkm_plan* p) { return p->T1f; }
 template <> inline cdf* ws3<df>(atkm_plan* p) { return reinterpret_cast<cdf*>(p->T1); }
-template <typename R> inline const R* u0tab(atkm_plan* p);
-template <> inline const double* u0tab<double>(atkm_plan* p) { return p->U0; }
-template <> inline const float* u0tab<float>(atkm_plan* p) { return p->U0f; }
-template <> inline const df* u0tab<df>(atkm_plan* p) { return p->U0d; }
+// z-pass multiplier: the plan's table (FP64, double-word) or the U0 octant
+// it is formed from in the pass (FP32); see OpAtkmZ.
+template <typename R> inline const R* kztab(atkm_plan* p);
+template <> inline const double* kztab<double>(atkm_plan* p) { return p->Kz; }
+template <> inline const float* kztab<float>(atkm_plan* p) { return p->U0f; }
+template <> inline const df* kztab<df>(atkm_plan* p) { return p->Kzd; }
 
 template <typename R> inline const char* nm(const char* d, const char* f, const char* w) {
   return std::is_same<R, double>::value ? d : (std::is_same<R, float>::value ? f : w);
@@ -45,8 +47,8 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
   const Geo& g = p->g;
   cx<R>* W1 = ws1<R>(p);
   cx<R>* W2 = ws2<R>(p);
-  const R* U0 = u0tab<R>(p);
-  if (!W1 || !W2 || !U0) return cudaErrorInvalidValue;
+  const R* K = kztab<R>(p);
+  if (!W1 || !W2 || !K) return cudaErrorInvalidValue;
   const Cst<R> c = make_cst<R>(g);
   const cx<R>* twM = tw_table_host<R>(p->fM[0]);
   const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
@@ -54,7 +56,9 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
   const double inb = mode == SRC_RHO ? 8.0 : (mode == SRC_PSI ? 16.0 : 32.0);
   const double fx = (double)g.Nz * g.Ny * fftflops(g.Nx), fy = (double)g.Nz * g.Xh * fftflops(g.My);
   const double fz = 2.0 * g.My * g.Xh * fftflops(g.Mz);
-  const double u0b = (double)sizeof(R) * (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
+  // multiplier: the table read once, or the U0 octant
+  const double kb = OpAtkmZ<R>::kTable ? (double)sizeof(R) * g.Mz * g.My * g.Xh
+                                       : (double)sizeof(R) * (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
   const long nl = (long)g.Nz * g.Ny;
   // x forward (real data: complex FFT of length Nx + post-twist)
   const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
@@ -77,11 +81,11 @@ cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b
   }
   // z forward * K_sym * inverse
   {
-    OpAtkmZ<R> op; op.W2 = W2; op.U0 = U0; op.c = c; op.XS = g.XS;
+    OpAtkmZ<R> op; op.W2 = W2; op.K = K; op.U0 = K; op.c = c; op.XS = g.XS;
     op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
     op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
     const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Xh, g.My);
-    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * H1 * s + u0b, fz, op, p->fM[2], pg);
+    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * H1 * s + kb, fz, op, p->fM[2], pg);
   }
   // y inverse
   {

@@ -106,8 +106,9 @@ struct GLNodes {
   double w[kGL];  // weights for (0, 1)
 };
 
-// Twiddles e^{-2 pi i m / L}.
-__global__ void k_twiddles(double2* t64, float2* t32, cdf* tdf, int L) {
+// Twiddles e^{-2 pi i m / L}, and the binary64 ones in multiply-add form
+// (lf_cform).
+__global__ void k_twiddles(double2* t64, float2* t32, cdf* tdf, double2* lf, int L) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < L; m += gridDim.x * blockDim.x) {
     double s, c;
     sincospi(2.0 * (double)m / (double)L, &s, &c);
@@ -117,6 +118,7 @@ __global__ void k_twiddles(double2* t64, float2* t32, cdf* tdf, int L) {
     w.x = df(c);
     w.y = df(-s);
     tdf[m] = w;
+    lf[m] = lf_cform(m, L) ? make_double2(c, -s / c) : make_double2(-s, c / -s);
   }
 }
 
@@ -200,6 +202,40 @@ __global__ void k_multiplier_full(double* __restrict__ K, const double* __restri
   }
 }
 
+// The multiplier of the z pass on the Nx + 1 half-spectrum columns, with the
+// inverse transform's 1 / (Mx My Mz) folded in.  A real density's spectrum is
+// Hermitian, so the real-data ATKM uses the symmetrised multiplier
+// K_sym(k) = (K(k) + K(-k)) / 2 = -1 + 3 U0(nu_k) (A^2 + B^2), where A sums
+// n_a nu_a over the axes whose index is not the padded Nyquist index M_a / 2
+// and B over those that are: the index of -k has the same Nyquist components
+// and the others negated, so the cross term 2AB cancels in the average (the
+// Nyquist index M_a / 2 stands for nu = -pi M_a / (4 L_a)).  Layout
+// [Mz][My][XS], columns x > Nx zero.
+__global__ void k_multiplier_half(double* __restrict__ Kh, const double* __restrict__ U0, Geo g, double n0,
+                                  double n1, double n2) {
+  const size_t total = (size_t)g.Mz * g.My * g.XS;
+  const double px = kPi / (2.0 * g.Lx), py = kPi / (2.0 * g.Ly), pz = kPi / (2.0 * g.Lz);
+  const double invM = 1.0 / ((double)g.Mx * g.My * g.Mz);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.XS);
+    const int o = (int)((i / g.XS) % g.My);
+    const int k = (int)(i / ((size_t)g.XS * g.My));
+    if (x > g.Nx) {
+      Kh[i] = 0.0;
+      continue;
+    }
+    const int kx = x == g.Nx ? -g.Nx : x;
+    const int ky = o < g.My / 2 ? o : o - g.My, kz = k < g.Mz / 2 ? k : k - g.Mz;
+    const double tx = n0 * (kx * px), ty = n1 * (ky * py), tz = n2 * (kz * pz);
+    double A = 0.0, B = 0.0;
+    if (x == g.Nx) B += tx; else A += tx;
+    if (o == g.Ny) B += ty; else A += ty;
+    if (k == g.Nz) B += tz; else A += tz;
+    const double u = U0[((size_t)abs(kz) * (g.Ny + 1) + abs(ky)) * (g.Nx + 1) + x];
+    Kh[i] = (3.0 * u * (A * A + B * B) - 1.0) * invM;
+  }
+}
+
 __global__ void k_to_f32(float* __restrict__ dst, const double* __restrict__ src, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -252,7 +288,7 @@ bool make_fft_len(int L, FftLen& f) {
 }
 
 void free_plan_memory(atkm_plan* p) {
-  void* ptrs[] = {p->tw64, p->tw32, p->twdf, p->U0, p->U0f, p->U0d, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f,
+  void* ptrs[] = {p->tw64, p->tw32, p->twdf, p->lf64, p->U0, p->U0f, p->Kz, p->Kzd, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f,
                   p->partials, p->scal};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -408,7 +444,8 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   cudaStream_t st = (cudaStream_t)stream;
   atkm_plan* p = new atkm_plan();
   memset(&p->g, 0, sizeof(p->g));
-  p->tw64 = nullptr; p->tw32 = nullptr; p->twdf = nullptr; p->U0 = nullptr; p->U0f = nullptr; p->U0d = nullptr;
+  p->tw64 = nullptr; p->tw32 = nullptr; p->twdf = nullptr; p->lf64 = nullptr; p->U0 = nullptr;
+  p->U0f = nullptr; p->Kz = nullptr; p->Kzd = nullptr;
   p->W1 = p->W2 = p->T1 = nullptr;
   p->W1f = p->W2f = p->T1f = nullptr; p->partials = nullptr; p->scal = nullptr; p->scal_host = nullptr;
   p->pcg = nullptr; p->prof = nullptr; p->prof_stopped_ = nullptr; p->bytes = 0; p->flags = flags;
@@ -435,6 +472,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   if ((e = dev_alloc(p, (void**)&p->tw64, twtot * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
   if ((e = dev_alloc(p, (void**)&p->tw32, twtot * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
   if ((e = dev_alloc(p, (void**)&p->twdf, twtot * sizeof(cdf))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
+  if ((e = dev_alloc(p, (void**)&p->lf64, twtot * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan twiddles"));
   size_t off = 0;
   for (int i = 0; i < 6; ++i) {
     FftLen& f = (i < 3) ? p->fN[i] : p->fM[i - 3];
@@ -442,7 +480,9 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
     f.tw64 = p->tw64 + off;
     f.tw32 = p->tw32 + off;
     f.twdf = p->twdf + off;
-    k_twiddles<<<(lens[i] + 255) / 256, 256, 0, st>>>(p->tw64 + off, p->tw32 + off, p->twdf + off, lens[i]);
+    f.lf64 = p->lf64 + off;
+    k_twiddles<<<(lens[i] + 255) / 256, 256, 0, st>>>(p->tw64 + off, p->tw32 + off, p->twdf + off, p->lf64 + off,
+                                                      lens[i]);
     count_launches(1);
     off += lens[i];
   }
@@ -494,6 +534,13 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   free_tmp();
   if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan U0 precompute"));
+  // ---- z-pass multiplier on the half spectrum (FP64; copies below)
+  const size_t n_kz = (size_t)g.Mz * g.My * g.XS;
+  if ((e = dev_alloc(p, (void**)&p->Kz, n_kz * sizeof(double))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan Kz"));
+  k_multiplier_half<<<(int)std::min<size_t>((n_kz + 255) / 256, 4096), 256, 0, st>>>(p->Kz, p->U0, g, p->n[0], p->n[1],
+                                                                                     p->n[2]);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan Kz"));
   // ---- workspaces
   const size_t Nt = (size_t)g.Nx * g.Ny * g.Nz;
   const size_t n_w1 = (size_t)g.Nz * g.Ny * g.XS, n_w2 = (size_t)g.Nz * g.My * g.XS;
@@ -509,8 +556,8 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
     count_launches(1);
   }
   if (flags & ATKM_PLAN_DF32) {
-    if ((e = dev_alloc(p, (void**)&p->U0d, n_oct * sizeof(df))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan U0d"));
-    k_to_df<<<(int)std::min<size_t>((n_oct + 255) / 256, 4096), 256, 0, st>>>(p->U0d, p->U0, n_oct);
+    if ((e = dev_alloc(p, (void**)&p->Kzd, n_kz * sizeof(df))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan Kzd"));
+    k_to_df<<<(int)std::min<size_t>((n_kz + 255) / 256, 4096), 256, 0, st>>>(p->Kzd, p->Kz, n_kz);
     count_launches(1);
   }
   // reductions: the largest CTA count of a reducing pass, or the vector grid

@@ -92,6 +92,21 @@ def _state(N, L, gamma, seed):
 
 @pytest.mark.parametrize("N,L,n", SMALL_CASES)
 def test_apply_H_energy_and_preconditioner_parity(lib, N, L, n):
+    _check_H_energy_P(lib, N, L, n)
+
+
+# Unpadded line lengths 16 ... 1024 of the fast engine in each axis role of
+# the H and preconditioner passes (x: N_x, y: N_y, z: N_z).
+H_FAST_LENGTH_GRIDS = [(1024, 16, 32), (32, 1024, 16), (16, 32, 1024), (512, 64, 16), (16, 512, 64),
+                       (64, 16, 512), (128, 256, 16), (16, 16, 256), (32, 32, 128)]
+
+
+@pytest.mark.parametrize("N", H_FAST_LENGTH_GRIDS)
+def test_H_and_preconditioner_every_fast_length(lib, N):
+    _check_H_energy_P(lib, N, (4.0, 3.0, 2.0), (0.6, 0.0, 0.8))
+
+
+def _check_H_energy_P(lib, N, L, n):
     gamma, beta, lam, Om = (1.0, 1.3, 6.0), 40.0, -12.0, 0.55
     plan = lib.Plan(N, L, n)
     oplan = O.Plan(N, L, n)
@@ -231,6 +246,42 @@ def test_df32_atkm_matches_oracle(lib, N, L, n):
     assert rel2(got, oplan.dipolar_potential(np.abs(a) ** 2)) <= 1e-11
     with pytest.raises(lib.AtkmError):
         lib.Plan(N, L, n).dipolar_potential_from_psi(dev(psi), df32=True)
+
+
+# Every power-of-two line length of the fast FFT engine (16 ... 1024) in each
+# role: x pass L = N_x, y pass L = 2 N_y, z pass L = 2 N_z.  The ATKM passes
+# skip the zero upper half of a forward transform's input and form only the
+# lower half of a cropped inverse transform's output; the stage structure
+# (one to three radix-8 stages, then a radix-2 or radix-4 tail or none)
+# differs between these lengths.
+FAST_LENGTH_CASES = [
+    ((1024, 16, 32), (0.6, 0.0, 0.8)),   # x 1024, y 32, z 64
+    ((512, 32, 8), (0.5, 0.5, math.sqrt(0.5))),  # x 512, y 64, z 16
+    ((256, 16, 128), (0.0, 0.6, 0.8)),   # x 256, y 32, z 256
+    ((128, 512, 8), (0.6, 0.0, 0.8)),    # x 128, y 1024, z 16
+    ((64, 256, 16), (0.5, 0.5, math.sqrt(0.5))),  # x 64, y 512, z 32
+    ((32, 128, 64), (0.0, 0.0, 1.0)),    # x 32, y 256, z 128
+    ((16, 64, 256), (0.6, 0.0, 0.8)),    # x 16, y 128, z 512
+    ((16, 8, 512), (0.5, 0.5, math.sqrt(0.5))),  # x 16, y 16, z 1024
+]
+
+
+@pytest.mark.parametrize("N,n", FAST_LENGTH_CASES)
+def test_atkm_every_fast_length_matches_oracle(lib, N, n):
+    L = (4.0, 3.0, 2.0)
+    plan = lib.Plan(N, L, n, f32=True, df32=True)
+    oplan = O.Plan(N, L, n)
+    shape = (N[2], N[1], N[0])
+    psi = W.random_smooth_field(N, L, (1.0, 1.3, 2.0), seed=401)
+    white = W.random_field(shape, 402)
+    for f in (psi, white):
+        ref = oplan.dipolar_potential(np.abs(f) ** 2)
+        assert rel2(host(plan.dipolar_potential_from_psi(dev(f))), ref) <= 1e-11
+        assert rel2(host(plan.dipolar_potential_from_psi(dev(f), df32=True)), ref) <= 1e-11
+        assert rel2(host(plan.dipolar_potential_from_psi(dev(f), f32=True)), ref) <= 5e-6
+    b = W.random_field(shape, 403)
+    got = host(plan.dipolar_potential_from_pair(dev(white), dev(b)))
+    assert rel2(got, oplan.dipolar_potential(np.real(np.conj(white) * b))) <= 1e-11
 
 
 def test_f32_atkm_close_to_oracle(lib):
