@@ -397,6 +397,8 @@ struct atkm_plan {
   double* U0;          // octant (Nz+1)(Ny+1)(Nx+1)
   float* U0f;          // FP32 copy of U0 (FP32 workspaces only)
   double* Kz;          // z-pass multiplier K_sym / (Mx My Mz), [Mz][My][XS] half spectrum
+  double* axtab;       // per-axis tables (AxT): for a = x, y, z five arrays of N_a doubles
+  double* Pw;          // [Nz][Ny][Nx] preconditioner weights, binary64 passes
   atkm::df* Kzd;       // double-word copy of Kz (ATKM_PLAN_DF32 only)
   atkm::cdf* twdf;     // double-word twiddle pool
   double2* W1;         // [Nz][Ny][XS] half spectrum in x

@@ -40,6 +40,19 @@ template <typename R> inline Cst<R> make_cst(const Geo& g) {
   return c;
 }
 
+// Per-axis tables of a plan (binary64, length N_a each), used by the binary64
+// H and preconditioner passes instead of forming the same values from integer
+// indices at every grid point (each index conversion and product is an
+// FP64-pipe instruction there): nu_k / N_a, (nu_k^2 / 2) / N_a, nu_k^2 / 2,
+// the coordinate -L_a + i h_a and half its square.
+struct AxT {
+  const double* nuN;
+  const double* kinN;
+  const double* hnu2;
+  const double* xc;
+  const double* hxc2;
+};
+
 template <typename R> struct PhysR {
   R gx2, gy2, gz2, beta, lambda, Omega;
 };
@@ -596,10 +609,20 @@ template <typename R> struct OpAtkmXI : OpBase<1, false, 0, true> {
 // ---- H_phi f (unpadded grid); acc: [Nz][Ny][Nx] kinetic+rotation accumulator.
 // x: multiplier nu^2/2 + Omega y nu on lines o = z Ny + y.
 template <typename R, bool RED> struct OpHX : OpBase<-1, true, RED ? 2 : 0, true> {
-  const double2* f; cx<R>* acc; Cst<R> c; R Omega;
+  const double2* f; cx<R>* acc; Cst<R> c; R Omega; AxT ax, ay;
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
   __device__ cx<R> load(int o, int, int pos) const { return from64<R>(f[(size_t)o * c.Nx + pos]); }
   __device__ void spectral(int o, int, int k, cx<R>& v, R* a) const {
+    if constexpr (std::is_same<R, double>::value) {
+      const double kin = ax.kinN[k], rot = Omega * ay.xc[o % c.Ny] * ax.nuN[k];
+      if (RED) {
+        const double a2 = v.x * v.x + v.y * v.y;
+        a[0] += kin * a2;
+        a[1] += rot * a2;
+      }
+      v = scl<R>(v, kin + rot);
+      return;
+    }
     const R invL = (R)1 / (R)c.Nx;
     const R nu = (R)kfreq(k, c.Nx) * c.kx;
     const R y = -c.Ly + (R)(o % c.Ny) * c.hy;
@@ -616,10 +639,20 @@ template <typename R, bool RED> struct OpHX : OpBase<-1, true, RED ? 2 : 0, true
 
 // y: multiplier nu^2/2 - Omega x nu on lines (o = z, x); acc += result.
 template <typename R, bool RED> struct OpHY : OpBase<-1, true, RED ? 2 : 0, false> {
-  const double2* f; cx<R>* acc; Cst<R> c; R Omega;
+  const double2* f; cx<R>* acc; Cst<R> c; R Omega; AxT ax, ay;
   __device__ bool valid(int, int x) const { return x < c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)o * c.Ny + pos) * c.Nx + x]); }
   __device__ void spectral(int, int x, int k, cx<R>& v, R* a) const {
+    if constexpr (std::is_same<R, double>::value) {
+      const double kin = ay.kinN[k], rot = -Omega * ax.xc[x] * ay.nuN[k];
+      if (RED) {
+        const double a2 = v.x * v.x + v.y * v.y;
+        a[0] += kin * a2;
+        a[1] += rot * a2;
+      }
+      v = scl<R>(v, kin + rot);
+      return;
+    }
     const R invL = (R)1 / (R)c.Ny;
     const R nu = (R)kfreq(k, c.Ny) * c.ky;
     const R xc = -c.Lx + (R)x * c.hx;
@@ -642,10 +675,17 @@ template <typename R, bool RED> struct OpHY : OpBase<-1, true, RED ? 2 : 0, fals
 // Reductions: kin_z, sum V|f|^2, sum |f|^4, sum Phi |f|^2, sum Re(Hf conj f), sum |f|^2.
 template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, false> {
   const double2* f; const double2* phi; const double* Phi; const cx<R>* acc; double2* Hf; Cst<R> c; PhysR<R> ph;
+  AxT ax, ay, az;
   bool same = false;  // f == phi (H phi): phi is not read a second time
   __device__ bool valid(int, int x) const { return x < c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)pos * c.Ny + o) * c.Nx + x]); }
   __device__ void spectral(int, int, int k, cx<R>& v, R* a) const {
+    if constexpr (std::is_same<R, double>::value) {
+      const double m = az.kinN[k];
+      if (RED) a[0] += m * (v.x * v.x + v.y * v.y);
+      v = scl<R>(v, m);
+      return;
+    }
     const R invL = (R)1 / (R)c.Nz;
     const R nu = (R)kfreq(k, c.Nz) * c.kz;
     const R m = (R)0.5 * nu * nu;
@@ -654,8 +694,13 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R* a) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
-    const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
-    const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
+    R V;
+    if constexpr (std::is_same<R, double>::value) {
+      V = ph.gz2 * az.hxc2[pos] + (ph.gy2 * ay.hxc2[o] + ph.gx2 * ax.hxc2[x]);
+    } else {
+      const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
+      V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
+    }
     const cx<R> fv = from64<R>(f[idx]);
     const cx<R> pv = same ? fv : from64<R>(phi[idx]);
     const R Pd = tor<R>(Phi[idx]);
@@ -686,11 +731,24 @@ __device__ __forceinline__ R pv_rsqrt(const Cst<R>& c, const PhysR<R>& ph, R alp
   return rsq<R>(den);
 }
 
+// Binary64: the weight P_V^{-1/2} of each point is also stored in Pw for the
+// x inverse pass, which then reads it instead of forming it again.
 template <typename R> struct OpPXF : OpBase<-1, false, 0, true> {
   const double2* r; const double2* phi; const double* Phi; cx<R>* Wk; Cst<R> c; PhysR<R> ph; const double* alpha;
+  AxT ax, ay, az; double* Pw;
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
   __device__ cx<R> load(int o, int, int pos) const {
     const size_t idx = (size_t)o * c.Nx + pos;
+    if constexpr (std::is_same<R, double>::value) {
+      const int y = o % c.Ny, z = o / c.Ny;
+      const double V = ph.gx2 * ax.hxc2[pos] + (ph.gy2 * ay.hxc2[y] + ph.gz2 * az.hxc2[z]);
+      const double2 pv = phi[idx];
+      const double Pd = Phi[idx];
+      const double den = *alpha + V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + fabs(ph.lambda) * (Pd > 0.0 ? Pd : 0.0);
+      const double w = rsqrt(den);
+      Pw[idx] = w;
+      return scl<R>(r[idx], w);
+    }
     const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
     return scl<R>(from64<R>(r[idx]), w);
   }
@@ -708,10 +766,15 @@ template <typename R, int S> struct OpPY : OpBase<S, false, 0, false> {
 
 // z forward * 1/((alpha + |nu|^2/2) N) * inverse on lines (o = y, x).
 template <typename R> struct OpPZ : OpBase<-1, true, 0, false> {
-  cx<R>* Wk; Cst<R> c; const double* alpha;
+  cx<R>* Wk; Cst<R> c; const double* alpha; AxT ax, ay, az;
   __device__ bool valid(int, int x) const { return x < c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const { return Wk[((size_t)pos * c.Ny + o) * c.Nx + x]; }
   __device__ void spectral(int o, int x, int k, cx<R>& v, R*) const {
+    if constexpr (std::is_same<R, double>::value) {
+      const double invN = 1.0 / ((double)c.Nx * (double)c.Ny * (double)c.Nz);
+      v = scl<R>(v, invN / (*alpha + (ax.hnu2[x] + ay.hnu2[o]) + az.hnu2[k]));
+      return;
+    }
     const R invN = (R)1 / ((R)c.Nx * (R)c.Ny * (R)c.Nz);
     const R nux = (R)kfreq(x, c.Nx) * c.kx, nuy = (R)kfreq(o, c.Ny) * c.ky, nuz = (R)kfreq(k, c.Nz) * c.kz;
     v = scl<R>(v, invN / (tor<R>(*alpha) + (R)0.5 * (nux * nux + nuy * nuy + nuz * nuz)));
@@ -721,11 +784,17 @@ template <typename R> struct OpPZ : OpBase<-1, true, 0, false> {
 
 template <typename R> struct OpPXI : OpBase<1, false, 0, true> {
   const cx<R>* Wk; const double2* phi; const double* Phi; double2* Pr; Cst<R> c; PhysR<R> ph; const double* alpha;
+  const double* Pw;  // binary64: the weights the x forward pass stored
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
   __device__ cx<R> load(int o, int, int pos) const { return Wk[(size_t)o * c.Nx + pos]; }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
   __device__ void store(int o, int, int pos, cx<R> v, R*) const {
     const size_t idx = (size_t)o * c.Nx + pos;
+    if constexpr (std::is_same<R, double>::value) {
+      const double w = Pw[idx];
+      Pr[idx] = make_double2(w * v.x, w * v.y);
+      return;
+    }
     const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
     Pr[idx] = make_double2(tod<R>(w * v.x), tod<R>(w * v.y));
   }

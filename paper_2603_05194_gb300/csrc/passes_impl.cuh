@@ -42,6 +42,18 @@ inline double fftflops(double n) { return 5.0 * n * log2(n); }
     if (e_ != cudaSuccess) return e_;                          \
   } while (0)
 
+// The plan's tables of axis a (0, 1, 2 = x, y, z); see AxT.
+inline AxT axt(const atkm_plan* p, int a) {
+  const int Ns[3] = {p->g.Nx, p->g.Ny, p->g.Nz};
+  size_t off = 0;
+  for (int b = 0; b < a; ++b) off += 5 * (size_t)Ns[b];
+  const double* t = p->axtab + off;
+  const size_t n = (size_t)Ns[a];
+  AxT r;
+  r.nuN = t; r.kinN = t + n; r.hnu2 = t + 2 * n; r.xc = t + 3 * n; r.hxc2 = t + 4 * n;
+  return r;
+}
+
 template <typename R>
 cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b, double* phi, cudaStream_t st) {
   const Geo& g = p->g;
@@ -124,12 +136,12 @@ cudaError_t h_pass_x(atkm_plan* p, const Phys& ph, const double* f, const double
     const double fl = 2.0 * nl * fftflops(g.Nx);
     const char* n = nm<R>("H_x_f64", "H_x_f32", "H_x_df");
     if (red) {
-      OpHX<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      OpHX<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega; op.ax = axt(p, 0); op.ay = axt(p, 1);
       op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
       ATKM_RUN(n, 16 * N + N * s, fl, op, p->fN[0], pg);
       if ((e = launch_finalize(p, 2, pg.grid.x * pg.grid.y, red_slot + 0, st)) != cudaSuccess) return e;
     } else {
-      OpHX<R, false> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      OpHX<R, false> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega; op.ax = axt(p, 0); op.ay = axt(p, 1);
       ATKM_RUN(n, 16 * N + N * s, fl, op, p->fN[0], pg);
     }
   }
@@ -158,12 +170,12 @@ cudaError_t h_pass_y(atkm_plan* p, const Phys& ph, const double* f, const double
     const double fl = 2.0 * g.Nz * g.Nx * fftflops(g.Ny);
     const char* n = nm<R>("H_y_f64", "H_y_f32", "H_y_df");
     if (red) {
-      OpHY<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      OpHY<R, true> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega; op.ax = axt(p, 0); op.ay = axt(p, 1);
       op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
       ATKM_RUN(n, 16 * N + 2 * N * s, fl, op, p->fN[1], pg);
       if ((e = launch_finalize(p, 2, pg.grid.x * pg.grid.y, red_slot + 2, st)) != cudaSuccess) return e;
     } else {
-      OpHY<R, false> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega;
+      OpHY<R, false> op; op.f = fin; op.acc = acc; op.c = c; op.Omega = pr.Omega; op.ax = axt(p, 0); op.ay = axt(p, 1);
       ATKM_RUN(n, 16 * N + 2 * N * s, fl, op, p->fN[1], pg);
     }
   }
@@ -193,12 +205,14 @@ cudaError_t h_pass_z(atkm_plan* p, const Phys& ph, const double* f, const double
     const char* n = nm<R>("H_z_f64", "H_z_f32", "H_z_df");
     if (red) {
       OpHZ<R, true> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
+      op.ax = axt(p, 0); op.ay = axt(p, 1); op.az = axt(p, 2);
       op.same = fin == pin;
       op.part = p->partials; op.pstride = pg.grid.x * pg.grid.y;
       ATKM_RUN(n, (op.same ? 40 : 56) * N + N * s, fl, op, p->fN[2], pg);
       if ((e = launch_finalize(p, 6, pg.grid.x * pg.grid.y, red_slot + 4, st)) != cudaSuccess) return e;
     } else {
       OpHZ<R, false> op; op.f = fin; op.phi = pin; op.Phi = Phi; op.acc = acc; op.Hf = out; op.c = c; op.ph = pr;
+      op.ax = axt(p, 0); op.ay = axt(p, 1); op.az = axt(p, 2);
       op.same = fin == pin;
       ATKM_RUN(n, (op.same ? 40 : 56) * N + N * s, fl, op, p->fN[2], pg);
     }
@@ -232,14 +246,17 @@ cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev
   {
     OpPXF<R> op; op.r = reinterpret_cast<const double2*>(r); op.phi = reinterpret_cast<const double2*>(phi);
     op.Phi = Phi; op.Wk = Wk; op.c = c; op.ph = pr; op.alpha = alpha_dev;
-    ATKM_RUN(nm<R>("P_x_fwd_f64", "P_x_fwd_f32", "P_x_fwd_df"), 40 * N + N * s, fx, op, p->fN[0], gx);
+    op.ax = axt(p, 0); op.ay = axt(p, 1); op.az = axt(p, 2); op.Pw = p->Pw;
+    // binary64 also writes the weights (8 B a point)
+    const double by = (std::is_same<R, double>::value ? 48.0 : 40.0) * N + N * s;
+    ATKM_RUN(nm<R>("P_x_fwd_f64", "P_x_fwd_f32", "P_x_fwd_df"), by, fx, op, p->fN[0], gx);
   }
   {
     OpPY<R, -1> op; op.Wk = Wk; op.c = c;
     ATKM_RUN(nm<R>("P_y_f64", "P_y_f32", "P_y_df"), 2 * N * s, fy, op, p->fN[1], gy);
   }
   {
-    OpPZ<R> op; op.Wk = Wk; op.c = c; op.alpha = alpha_dev;
+    OpPZ<R> op; op.Wk = Wk; op.c = c; op.alpha = alpha_dev; op.ax = axt(p, 0); op.ay = axt(p, 1); op.az = axt(p, 2);
     ATKM_RUN(nm<R>("P_z_f64", "P_z_f32", "P_z_df"), 2 * N * s, 2.0 * g.Ny * g.Nx * fftflops(g.Nz), op, p->fN[2], gz);
   }
   {
@@ -248,8 +265,10 @@ cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev
   }
   {
     OpPXI<R> op; op.Wk = Wk; op.phi = reinterpret_cast<const double2*>(phi); op.Phi = Phi;
-    op.Pr = reinterpret_cast<double2*>(Pr); op.c = c; op.ph = pr; op.alpha = alpha_dev;
-    ATKM_RUN(nm<R>("P_x_inv_f64", "P_x_inv_f32", "P_x_inv_df"), 40 * N + N * s, fx, op, p->fN[0], gx);
+    op.Pr = reinterpret_cast<double2*>(Pr); op.c = c; op.ph = pr; op.alpha = alpha_dev; op.Pw = p->Pw;
+    // binary64 reads the stored weights (8 B) instead of phi and Phi (24 B)
+    const double by = (std::is_same<R, double>::value ? 24.0 : 40.0) * N + N * s;
+    ATKM_RUN(nm<R>("P_x_inv_f64", "P_x_inv_f32", "P_x_inv_df"), by, fx, op, p->fN[0], gx);
   }
   return cudaSuccess;
 }

@@ -288,7 +288,7 @@ bool make_fft_len(int L, FftLen& f) {
 }
 
 void free_plan_memory(atkm_plan* p) {
-  void* ptrs[] = {p->tw64, p->tw32, p->twdf, p->lf64, p->U0, p->U0f, p->Kz, p->Kzd, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f,
+  void* ptrs[] = {p->tw64, p->tw32, p->twdf, p->lf64, p->axtab, p->Pw, p->U0, p->U0f, p->Kz, p->Kzd, p->W1, p->W2, p->T1, p->W1f, p->W2f, p->T1f,
                   p->partials, p->scal};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -445,6 +445,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   atkm_plan* p = new atkm_plan();
   memset(&p->g, 0, sizeof(p->g));
   p->tw64 = nullptr; p->tw32 = nullptr; p->twdf = nullptr; p->lf64 = nullptr; p->U0 = nullptr;
+  p->axtab = nullptr; p->Pw = nullptr;
   p->U0f = nullptr; p->Kz = nullptr; p->Kzd = nullptr;
   p->W1 = p->W2 = p->T1 = nullptr;
   p->W1f = p->W2f = p->T1f = nullptr; p->partials = nullptr; p->scal = nullptr; p->scal_host = nullptr;
@@ -485,6 +486,35 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
                                                       lens[i]);
     count_launches(1);
     off += lens[i];
+  }
+  // ---- per-axis tables of the binary64 H and preconditioner passes (AxT):
+  // nu_k / N, (nu_k^2 / 2) / N, nu_k^2 / 2 with nu_k = k' pi / L (k' the signed
+  // index), and the coordinate x_i = -L + i h with x_i^2 / 2
+  {
+    const int Ns[3] = {g.Nx, g.Ny, g.Nz};
+    const double Ls[3] = {g.Lx, g.Ly, g.Lz}, hs[3] = {g.hx, g.hy, g.hz};
+    std::vector<double> tab;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int n = Ns[ax];
+      const double kap = kPi / Ls[ax], invn = 1.0 / (double)n;
+      std::vector<double> nuN(n), kinN(n), hnu2(n), xc(n), hxc2(n);
+      for (int k = 0; k < n; ++k) {
+        const int kk = k < n / 2 ? k : k - n;
+        const double nu = (double)kk * kap;
+        nuN[k] = nu * invn;
+        hnu2[k] = 0.5 * nu * nu;
+        kinN[k] = hnu2[k] * invn;
+        xc[k] = -Ls[ax] + (double)k * hs[ax];
+        hxc2[k] = 0.5 * xc[k] * xc[k];
+      }
+      for (auto* v : {&nuN, &kinN, &hnu2, &xc, &hxc2}) tab.insert(tab.end(), v->begin(), v->end());
+    }
+    if ((e = dev_alloc(p, (void**)&p->axtab, tab.size() * sizeof(double))) != cudaSuccess)
+      return bail(cuda_fail(nullptr, e, "plan axis tables"));
+    if ((e = cudaMemcpyAsync(p->axtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return bail(cuda_fail(nullptr, e, "plan axis tables"));
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan axis tables"));
   }
   // ---- U0 octant
   const double a[3] = {2.0 * L[0], 2.0 * L[1], 2.0 * L[2]};
@@ -547,6 +577,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   if ((e = dev_alloc(p, (void**)&p->W1, n_w1 * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
   if ((e = dev_alloc(p, (void**)&p->W2, n_w2 * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
   if ((e = dev_alloc(p, (void**)&p->T1, Nt * sizeof(double2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
+  if ((e = dev_alloc(p, (void**)&p->Pw, Nt * sizeof(double))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
   if (flags & ATKM_PLAN_F32) {
     if ((e = dev_alloc(p, (void**)&p->W1f, n_w1 * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
     if ((e = dev_alloc(p, (void**)&p->W2f, n_w2 * sizeof(float2))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan workspace"));
