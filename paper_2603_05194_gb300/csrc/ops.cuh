@@ -255,6 +255,7 @@ template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
   static constexpr bool kMirror = false;   // post-processing needs the mirror frequency L - k
   static constexpr bool kZeroUpper = false;  // positions >= L/2 of the first transform's input are zero
   static constexpr bool kHalfOut = false;    // only positions < L/2 of the last transform's output are used
+  static constexpr bool kNyqTail = false;    // column pass over columns 0..c.Nx (see k_fast)
   double* part = nullptr;                  // reduction partials [slot][block]
   int pstride = 0;
 };
@@ -284,9 +285,25 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : (std::is_same<R
   int t, j;
   if (Op::kLM) { t = threadIdx.x / C::TPL; j = threadIdx.x % C::TPL; }
   else { j = threadIdx.x / C::T; t = threadIdx.x % C::T; }
-  const int o = Op::kLM ? blockIdx.x * C::T + t : blockIdx.y;
-  const int x = Op::kLM ? 0 : blockIdx.x * C::T + t;
-  const bool ok = op.valid(o, x);
+  int o = Op::kLM ? blockIdx.x * C::T + t : blockIdx.y;
+  int x = Op::kLM ? 0 : blockIdx.x * C::T + t;
+  bool ok;
+  static_assert(!Op::kNyqTail || (Op::kRed == 0 && !Op::kLM), "the remapped CTAs that exit write no partial sums");
+  if constexpr (Op::kNyqTail) {
+    // Half-spectrum column passes (columns 0..Nx): when T divides Nx the last
+    // block column would carry column Nx alone; it takes column Nx of T
+    // consecutive rows instead, so that no CTA transforms idle columns.
+    if (blockIdx.x == gridDim.x - 1 && op.c.Nx % C::T == 0) {
+      if (blockIdx.y * C::T >= gridDim.y) return;  // whole CTA: before any barrier
+      x = op.c.Nx;
+      o = blockIdx.y * C::T + t;
+      ok = o < (int)gridDim.y && op.valid(o, x);
+    } else {
+      ok = op.valid(o, x);
+    }
+  } else {
+    ok = op.valid(o, x);
+  }
   cx<R> v[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) v[r] = (ok && (!Op::kZeroUpper || r < 4)) ? op.load(o, x, j + C::TPL * r) : czero<R>();
@@ -523,6 +540,7 @@ template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
 // y forward: o = z, x = kx in [0, Nx]; rows y < Ny of W1, zero beyond.
 template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
   static constexpr bool kZeroUpper = true;  // rows y >= Ny = L/2 are the padding
+  static constexpr bool kNyqTail = true;
   const cx<R>* W1; cx<R>* W2; Cst<R> c; int XS;
   __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const {
@@ -543,6 +561,7 @@ template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
 template <typename R> struct OpAtkmZ : OpBase<-1, true, 0, false> {
   static constexpr bool kZeroUpper = true;  // rows z >= Nz = L/2 are the padding
   static constexpr bool kHalfOut = true;    // only rows z < Nz are kept
+  static constexpr bool kNyqTail = true;
   static constexpr bool kTable = !std::is_same<R, float>::value;
   cx<R>* W2; const R* K; const R* U0; Cst<R> c; R n0, n1, n2, invM; int XS;
   __device__ bool valid(int, int x) const { return x <= c.Nx; }
@@ -572,6 +591,7 @@ template <typename R> struct OpAtkmZ : OpBase<-1, true, 0, false> {
 // y inverse: o = z, x = kx in [0, Nx]; output rows y < Ny into W1.
 template <typename R> struct OpAtkmYI : OpBase<1, false, 0, false> {
   static constexpr bool kHalfOut = true;  // only rows y < Ny = L/2 are kept
+  static constexpr bool kNyqTail = true;
   const cx<R>* W2; cx<R>* W1; Cst<R> c; int XS;
   __device__ bool valid(int, int x) const { return x <= c.Nx; }
   __device__ cx<R> load(int o, int x, int pos) const { return W2[((size_t)o * c.My + pos) * XS + x]; }

@@ -110,9 +110,21 @@ template <typename T, int NS> struct Sums {
 #pragma unroll
     for (int s = 0; s < NS; ++s) { d[s] = 0.0; f[s] = (T)0; }
   }
-  __device__ __forceinline__ void add(int s, T v) {
-    if constexpr (sizeof(T) == 8) d[s] += v;
-    else f[s] += v;
+  // sum_s += a b.  Binary64: one FMA (every instruction here is an FP64-pipe
+  // instruction, and these kernels are bound by that pipe).  FP32: the
+  // product, then the add.
+  __device__ __forceinline__ void mac(int s, T a, T b) {
+    if constexpr (sizeof(T) == 8) d[s] = fma(a, b, d[s]);
+    else f[s] += a * b;
+  }
+  // sum_s += Re(a conj b) = a.x b.x + a.y b.y: two FMAs in binary64
+  __device__ __forceinline__ void dot(int s, V2<T> a, V2<T> b) {
+    if constexpr (sizeof(T) == 8) {
+      d[s] = fma(a.x, b.x, d[s]);
+      d[s] = fma(a.y, b.y, d[s]);
+    } else {
+      f[s] += a.x * b.x + a.y * b.y;
+    }
   }
   __device__ __forceinline__ void flush() {
     if constexpr (sizeof(T) == 4) {
@@ -150,7 +162,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const double2* __restrict__
   Sums<double, 1> acc;
   ATKM_GRID_LOOP(j, N) {
     const double2 a = u[j], b = v[j];
-    acc.add(0, a.x * b.x + a.y * b.y);
+    acc.mac(0, a.x, b.x);
+    acc.mac(0, a.y, b.y);
   }
   acc.store(part);
 }
@@ -164,13 +177,13 @@ k_dir_dots(const double2* __restrict__ Pr, const double2* __restrict__ phi, cons
   Sums<T, 7> acc;
   ATKM_GRID_LOOP(j, N) {
     const V2<T> P = ld2<T>(Pr[j]), f = ld2<T>(phi[j]), a = ld2<T>(r[j]), b = ld2<T>(rp[j]), c = ld2<T>(pp[j]);
-    acc.add(0, dotr(P, f));
-    acc.add(1, dotr(a, P));
-    acc.add(2, dotr(a, f));
-    acc.add(3, dotr(b, P));
-    acc.add(4, dotr(b, f));
-    acc.add(5, dotr(c, f));
-    acc.add(6, dotr(f, f));
+    acc.dot(0, P, f);
+    acc.dot(1, a, P);
+    acc.dot(2, a, f);
+    acc.dot(3, b, P);
+    acc.dot(4, b, f);
+    acc.dot(5, c, f);
+    acc.dot(6, f, f);
     acc.next();
   }
   acc.store(part);
@@ -199,8 +212,8 @@ k_lincomb(double2* __restrict__ out, const double2* __restrict__ v0, Coef c0, co
     if (v1) { const V2<T> a = ld2<T>(v1[j]); o.x += a1 * a.x; o.y += a1 * a.y; }
     if (v2) { const V2<T> a = ld2<T>(v2[j]); o.x += a2 * a.x; o.y += a2 * a.y; }
     out[j] = make_double2(tod<T>(o.x), tod<T>(o.y));
-    acc.add(0, dotr(o, o));
-    if (w) acc.add(1, dotr(ld2<T>(w[j]), o));
+    acc.dot(0, o, o);
+    if (w) acc.dot(1, ld2<T>(w[j]), o);
     acc.next();
   }
   acc.store(part);
@@ -248,10 +261,10 @@ k_curv_sums(const double2* __restrict__ Hp, const double2* __restrict__ phi, con
     const V2<T> a = ld2<T>(phi[j]), b = ld2<T>(p[j]), h = ld2<T>(Hp[j]);
     const T rp = dotr(a, b);
     const T w = bt * dotr(a, a) + lm * ld1<T>(Phi[j]);
-    acc.add(0, dotr(h, b));
-    acc.add(1, rp * (bt * rp + lm * ld1<T>(Phi1[j])));
-    acc.add(2, w * rp);
-    acc.add(3, w * dotr(b, b));
+    acc.dot(0, h, b);
+    acc.mac(1, rp, bt * rp + lm * ld1<T>(Phi1[j]));
+    acc.mac(2, w, rp);
+    acc.mac(3, w, dotr(b, b));
     acc.next();
   }
   acc.store(part);
@@ -265,8 +278,8 @@ k_quartic_sums(const double2* __restrict__ phi, const double* __restrict__ Phi, 
   ATKM_GRID_LOOP(j, N) {
     const V2<T> a = ld2<T>(phi[j]);
     const T r = dotr(a, a);
-    acc.add(0, r * r);
-    acc.add(1, ld1<T>(Phi[j]) * r);
+    acc.mac(0, r, r);
+    acc.mac(1, ld1<T>(Phi[j]), r);
     acc.next();
   }
   acc.store(part);
