@@ -183,7 +183,8 @@ FP64_PEAK_GFLOPS = 1255.0
 # kernels on this workload (the profile file gives the command).  A kernel not
 # listed here reports traffic null.
 NCU_TRAFFIC = {
-    "H_z_f32": {"bytes": 172601344.0,
+    "atkm_z_f64": {"bytes": 374209280.0, "profile": "profiles/atkm_z_f64_256x256x64.md"},
+    "H_z_f32": {"bytes": 172407808.0,
                 "profile": "profiles/pcg_mixed_kernels_256x256x64.md (the H phi launch with energy sums)"},
 }
 
