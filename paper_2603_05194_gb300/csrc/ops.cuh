@@ -67,6 +67,15 @@ __device__ __forceinline__ int kfreq(int m, int M) { return m < (M >> 1) ? m : m
 __device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
 
 template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { return mk<R>(tor<R>(z.x), tor<R>(z.y)); }
+
+// Loads of a pass's read-only inputs through the non-coherent path, so that
+// the compiler may issue them ahead of the thread's earlier stores (a pass's
+// inputs never alias its outputs): an epilogue then waits for one memory
+// round trip, not one per element.
+__device__ __forceinline__ double2 ldro(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldro(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
+__device__ __forceinline__ cdf ldro(const cdf* p) { return *p; }
 template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R)0, (R)0); }
 
 template <typename R> __device__ __forceinline__ R rsq(R v);
@@ -721,11 +730,11 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
       const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
       V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
     }
-    const cx<R> fv = from64<R>(f[idx]);
-    const cx<R> pv = same ? fv : from64<R>(phi[idx]);
-    const R Pd = tor<R>(Phi[idx]);
+    const cx<R> fv = from64<R>(ldro(f + idx));
+    const cx<R> pv = same ? fv : from64<R>(ldro(phi + idx));
+    const R Pd = tor<R>(ldro(Phi + idx));
     const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
-    const cx<R> kin = add<R>(acc[idx], v);
+    const cx<R> kin = add<R>(ldro(acc + idx), v);
     const R ox = kin.x + w * fv.x, oy = kin.y + w * fv.y;
     Hf[idx] = make_double2(tod<R>(ox), tod<R>(oy));
     if (RED) {
@@ -811,11 +820,11 @@ template <typename R> struct OpPXI : OpBase<1, false, 0, true> {
   __device__ void store(int o, int, int pos, cx<R> v, R*) const {
     const size_t idx = (size_t)o * c.Nx + pos;
     if constexpr (std::is_same<R, double>::value) {
-      const double w = Pw[idx];
+      const double w = ldro(Pw + idx);
       Pr[idx] = make_double2(w * v.x, w * v.y);
       return;
     }
-    const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
+    const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, ldro(phi + idx), ldro(Phi + idx));
     Pr[idx] = make_double2(tod<R>(w * v.x), tod<R>(w * v.y));
   }
 };
