@@ -79,31 +79,31 @@ __device__ __forceinline__ df df_rsqrt(df v) {
   return y + y * (df(0.5f, 0.0f) * e);
 }
 
-// Complex operations are out-of-line functions: every butterfly and twiddle
-// of the FFT engine calls them, so each double-word kernel contains one copy
-// of their code instead of one per call site (a fully inlined instantiation
-// of the ATKM passes took minutes of nvcc time), at the price of a call.
-static __device__ __noinline__ cdf df_cadd(cdf a, cdf b) {
+// Complex operations, inlined at every butterfly and twiddle of the FFT
+// engine.  As out-of-line functions (one copy of their code per kernel) the
+// double-word ATKM compiled several times faster but ran at two thirds of
+// this speed: the passes are issue-bound and the calls cost instructions.
+static __device__ __forceinline__ cdf df_cadd(cdf a, cdf b) {
   cdf r;
   r.x = a.x + b.x;
   r.y = a.y + b.y;
   return r;
 }
-static __device__ __noinline__ cdf df_csub(cdf a, cdf b) {
+static __device__ __forceinline__ cdf df_csub(cdf a, cdf b) {
   cdf r;
   r.x = a.x - b.x;
   r.y = a.y - b.y;
   return r;
 }
 // a * b (conj_b = false) or a * conj(b) (conj_b = true)
-static __device__ __noinline__ cdf df_cmul(cdf a, cdf b, bool conj_b) {
+static __device__ __forceinline__ cdf df_cmul(cdf a, cdf b, bool conj_b) {
   const df by = conj_b ? -b.y : b.y;
   cdf r;
   r.x = a.x * b.x - a.y * by;
   r.y = a.x * by + a.y * b.x;
   return r;
 }
-static __device__ __noinline__ cdf df_cscl(cdf a, df s) {
+static __device__ __forceinline__ cdf df_cscl(cdf a, df s) {
   cdf r;
   r.x = a.x * s;
   r.y = a.y * s;
