@@ -285,7 +285,7 @@ __device__ __forceinline__ void reduce_out(R (&acc)[NR], double* part, int pstri
 }
 
 template <typename R, int L, class Op>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : (std::is_same<R, double>::value ? 2 : 1)) k_fast(Op op, const cx<R>* __restrict__ twg) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_fast(Op op, const cx<R>* __restrict__ twg) {
   using C = FastCfg<L>;
   extern __shared__ __align__(16) unsigned char fast_smem[];
   cx<R>* tw = reinterpret_cast<cx<R>*>(fast_smem);
