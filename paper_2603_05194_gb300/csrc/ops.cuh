@@ -75,7 +75,13 @@ template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { retur
 __device__ __forceinline__ double2 ldro(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ldro(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
-__device__ __forceinline__ cdf ldro(const cdf* p) { return *p; }
+__device__ __forceinline__ cdf ldro(const cdf* p) {  // (x.hi, x.lo, y.hi, y.lo), 16-byte aligned
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  cdf r;
+  r.x = df(t.x, t.y);
+  r.y = df(t.z, t.w);
+  return r;
+}
 template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R)0, (R)0); }
 
 template <typename R> __device__ __forceinline__ R rsq(R v);
