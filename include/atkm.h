@@ -63,9 +63,14 @@ typedef struct atkm_plan atkm_plan;
  *   flags ATKM_PLAN_F64, or any of ATKM_PLAN_F32 and ATKM_PLAN_DF32.
  * Builds, in FP64 on the device, U0(nu) = int_{D_2L} e^{-i nu.y}/(4 pi|y|) dy on
  * the nonnegative frequency octant of the twofold-padded grid (Eq. (FUk)),
- * from which the dipolar multiplier K = -1 + 3 (n.nu)^2 U0 is formed on the
- * fly.  Synchronises `stream` before returning.  On success *out owns all
- * device memory of the plan; on failure *out is NULL and nothing is leaked.
+ * and from it the dipolar multiplier K = -1 + 3 (n.nu)^2 U0, symmetrised on the
+ * padded Nyquist planes, on the half spectrum kept by the real-data transform
+ * (FP64, and a double-word copy with ATKM_PLAN_DF32; FP32 passes form it from
+ * an FP32 copy of U0).  Also holds the twiddle tables, per-axis frequency and
+ * coordinate tables and the workspaces (atkm_plan_device_bytes gives the
+ * total; about 1 GB at 256 x 256 x 64).  Synchronises `stream` before
+ * returning.  On success *out owns all device memory of the plan; on failure
+ * *out is NULL and nothing is leaked.
  */
 int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const double n[3],
                      unsigned flags, void* stream);
