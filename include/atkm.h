@@ -68,7 +68,8 @@ typedef struct atkm_plan atkm_plan;
  * (FP64, and a double-word copy with ATKM_PLAN_DF32; FP32 passes form it from
  * an FP32 copy of U0).  Also holds the twiddle tables, per-axis frequency and
  * coordinate tables and the workspaces (atkm_plan_device_bytes gives the
- * total; about 1 GB at 256 x 256 x 64).  Synchronises `stream` before
+ * total: about 0.5 GB for an FP64 plan at 256 x 256 x 64, more once a solve
+ * has allocated its vectors).  Synchronises `stream` before
  * returning.  On success *out owns all device memory of the plan; on failure
  * *out is NULL and nothing is leaked.
  */
