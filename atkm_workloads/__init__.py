@@ -248,7 +248,8 @@ def paper_guesses(N, L, gamma, beta, Omega) -> dict:
     (a) the unit-width Gaussian exp(-|x|^2/2); (b) (x + i y) times it; (c) a + b;
     (d) (1 - Omega) a + Omega b; (e) Omega a + (1 - Omega) b, each of b-e with
     its complex conjugate; (f) the Thomas-Fermi profile sqrt(max(mu_TF - V, 0)/beta)
-    with mu_TF = (1/2) (15 beta gamma_x gamma_y gamma_z / (4 pi))^(2/5)."""
+    with V = (gamma_x^2 x^2 + gamma_y^2 y^2 + gamma_z^2 z^2)/2 and
+    mu_TF = (1/2) (15 beta gamma_x gamma_y gamma_z / (4 pi))^(2/5)."""
     x, y, z = mesh(N, L)
     shape = (N[2], N[1], N[0])
 
@@ -258,7 +259,7 @@ def paper_guesses(N, L, gamma, beta, Omega) -> dict:
 
     pa = nrm(np.exp(-(x * x + y * y + z * z) / 2))
     pb = nrm((x + 1j * y) * pa)
-    V = 0.5 * (gamma[0] * x * x + gamma[1] * y * y + gamma[2] * z * z)
+    V = 0.5 * (gamma[0] ** 2 * x * x + gamma[1] ** 2 * y * y + gamma[2] ** 2 * z * z)  # the trap, Eq. (Vpoten)
     mu_tf = 0.5 * (15.0 * beta * gamma[0] * gamma[1] * gamma[2] / (4.0 * math.pi)) ** 0.4
     g = {"a": pa, "b": pb, "c": nrm(pa + pb), "d": nrm((1 - Omega) * pa + Omega * pb),
          "e": nrm(Omega * pa + (1 - Omega) * pb)}
