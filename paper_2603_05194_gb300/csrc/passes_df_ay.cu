@@ -1,0 +1,7 @@
+// Double-word instantiation of the ATKM y passes (see passes_df.cu).
+#include "passes_impl.cuh"
+
+namespace atkm {
+template cudaError_t atkm_pass_yf<df>(atkm_plan*, int, const double*, const double*, double*, cudaStream_t);
+template cudaError_t atkm_pass_yi<df>(atkm_plan*, int, const double*, const double*, double*, cudaStream_t);
+}  // namespace atkm

@@ -54,62 +54,125 @@ inline AxT axt(const atkm_plan* p, int a) {
   return r;
 }
 
-template <typename R>
-cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b, double* phi, cudaStream_t st) {
+// What every ATKM pass needs of the plan: workspaces, constants, the byte and
+// flop counts of the profiler.
+template <typename R> struct AtkmCtx {
+  const Geo* g;
+  cx<R>* W1;
+  cx<R>* W2;
+  const R* K;
+  Cst<R> c;
+  const cx<R>* twM;
+  double N, s, H1, fx, fy, fz, kb;
+  long nl;
+};
+template <typename R> inline AtkmCtx<R> atkm_ctx(atkm_plan* p) {
+  AtkmCtx<R> x;
   const Geo& g = p->g;
-  cx<R>* W1 = ws1<R>(p);
-  cx<R>* W2 = ws2<R>(p);
-  const R* K = kztab<R>(p);
-  if (!W1 || !W2 || !K) return cudaErrorInvalidValue;
-  const Cst<R> c = make_cst<R>(g);
-  const cx<R>* twM = tw_table_host<R>(p->fM[0]);
-  const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
-  const double H1 = (double)g.Nz * g.Ny * g.Xh;  // half-spectrum elements of W1
-  const double inb = mode == SRC_RHO ? 8.0 : (mode == SRC_PSI ? 16.0 : 32.0);
-  const double fx = (double)g.Nz * g.Ny * fftflops(g.Nx), fy = (double)g.Nz * g.Xh * fftflops(g.My);
-  const double fz = 2.0 * g.My * g.Xh * fftflops(g.Mz);
+  x.g = &g;
+  x.W1 = ws1<R>(p);
+  x.W2 = ws2<R>(p);
+  x.K = kztab<R>(p);
+  x.c = make_cst<R>(g);
+  x.twM = tw_table_host<R>(p->fM[0]);
+  x.N = (double)g.Nx * g.Ny * g.Nz;
+  x.s = (double)sizeof(cx<R>);
+  x.H1 = (double)g.Nz * g.Ny * g.Xh;  // half-spectrum elements of W1
+  x.fx = (double)g.Nz * g.Ny * fftflops(g.Nx);
+  x.fy = (double)g.Nz * g.Xh * fftflops(g.My);
+  x.fz = 2.0 * g.My * g.Xh * fftflops(g.Mz);
   // multiplier: the table read once, or the U0 octant
-  const double kb = OpAtkmZ<R>::kTable ? (double)sizeof(R) * g.Mz * g.My * g.Xh
-                                       : (double)sizeof(R) * (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
-  const long nl = (long)g.Nz * g.Ny;
-  // x forward (real data: complex FFT of length Nx + post-twist)
-  const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
+  x.kb = OpAtkmZ<R>::kTable ? (double)sizeof(R) * g.Mz * g.My * g.Xh
+                            : (double)sizeof(R) * (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
+  x.nl = (long)g.Nz * g.Ny;
+  return x;
+}
+
+// The five passes of one ATKM evaluation, each a function of its own (same
+// signature) so that heavy instantiations can compile in separate
+// translation units.
+// x forward (real data: complex FFT of length Nx + post-twist)
+template <typename R>
+cudaError_t atkm_pass_xf(atkm_plan* p, int mode, const double* a, const double* b, double*, cudaStream_t st) {
+  const AtkmCtx<R> x = atkm_ctx<R>(p);
+  const Geo& g = *x.g;
+  if (!x.W1) return cudaErrorInvalidValue;
+  const double inb = mode == SRC_RHO ? 8.0 : (mode == SRC_PSI ? 16.0 : 32.0);
+  const PassGrid gx = pass_grid<R>(g.Nx, true, x.nl, 0, 0);
   const char* nx = nm<R>("atkm_x_fwd_f64", "atkm_x_fwd_f32", "atkm_x_fwd_df");
   if (mode == SRC_RHO) {
-    OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
+    OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = x.W1; op.twM = x.twM; op.c = x.c; op.XS = g.XS;
+    ATKM_RUN(nx, inb * x.N + x.H1 * x.s, x.fx, op, p->fN[0], gx);
   } else if (mode == SRC_PSI) {
-    OpAtkmXF<R, SRC_PSI> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
+    OpAtkmXF<R, SRC_PSI> op; op.a = a; op.b = b; op.W1 = x.W1; op.twM = x.twM; op.c = x.c; op.XS = g.XS;
+    ATKM_RUN(nx, inb * x.N + x.H1 * x.s, x.fx, op, p->fN[0], gx);
   } else {
-    OpAtkmXF<R, SRC_PAIR> op; op.a = a; op.b = b; op.W1 = W1; op.twM = twM; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nx, inb * N + H1 * s, fx, op, p->fN[0], gx);
-  }
-  // y forward on the Nx + 1 half-spectrum columns
-  const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
-  {
-    OpAtkmYF<R> op; op.W1 = W1; op.W2 = W2; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32", "atkm_y_fwd_df"), 3 * H1 * s, fy, op, p->fM[1], gy);
-  }
-  // z forward * K_sym * inverse
-  {
-    OpAtkmZ<R> op; op.W2 = W2; op.K = K; op.U0 = K; op.c = c; op.XS = g.XS;
-    op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
-    op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
-    const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Xh, g.My);
-    ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * H1 * s + kb, fz, op, p->fM[2], pg);
-  }
-  // y inverse
-  {
-    OpAtkmYI<R> op; op.W2 = W2; op.W1 = W1; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32", "atkm_y_inv_df"), 3 * H1 * s, fy, op, p->fM[1], gy);
-  }
-  // x inverse (C2R) + crop
-  {
-    OpAtkmXI<R> op; op.W1 = W1; op.phi = phi; op.twM = twM; op.c = c; op.XS = g.XS;
-    ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32", "atkm_x_inv_df"), H1 * s + 8 * N, fx, op, p->fN[0], gx);
+    OpAtkmXF<R, SRC_PAIR> op; op.a = a; op.b = b; op.W1 = x.W1; op.twM = x.twM; op.c = x.c; op.XS = g.XS;
+    ATKM_RUN(nx, inb * x.N + x.H1 * x.s, x.fx, op, p->fN[0], gx);
   }
   return cudaSuccess;
+}
+
+// y forward on the Nx + 1 half-spectrum columns
+template <typename R>
+cudaError_t atkm_pass_yf(atkm_plan* p, int, const double*, const double*, double*, cudaStream_t st) {
+  const AtkmCtx<R> x = atkm_ctx<R>(p);
+  const Geo& g = *x.g;
+  if (!x.W1 || !x.W2) return cudaErrorInvalidValue;
+  const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
+  OpAtkmYF<R> op; op.W1 = x.W1; op.W2 = x.W2; op.c = x.c; op.XS = g.XS;
+  ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32", "atkm_y_fwd_df"), 3 * x.H1 * x.s, x.fy, op, p->fM[1], gy);
+  return cudaSuccess;
+}
+
+// z forward * K_sym * inverse
+template <typename R>
+cudaError_t atkm_pass_z(atkm_plan* p, int, const double*, const double*, double*, cudaStream_t st) {
+  const AtkmCtx<R> x = atkm_ctx<R>(p);
+  const Geo& g = *x.g;
+  if (!x.W2 || !x.K) return cudaErrorInvalidValue;
+  OpAtkmZ<R> op; op.W2 = x.W2; op.K = x.K; op.U0 = x.K; op.c = x.c; op.XS = g.XS;
+  op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
+  op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
+  const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Xh, g.My);
+  ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * x.H1 * x.s + x.kb, x.fz, op, p->fM[2], pg);
+  return cudaSuccess;
+}
+
+// y inverse
+template <typename R>
+cudaError_t atkm_pass_yi(atkm_plan* p, int, const double*, const double*, double*, cudaStream_t st) {
+  const AtkmCtx<R> x = atkm_ctx<R>(p);
+  const Geo& g = *x.g;
+  if (!x.W1 || !x.W2) return cudaErrorInvalidValue;
+  const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
+  OpAtkmYI<R> op; op.W2 = x.W2; op.W1 = x.W1; op.c = x.c; op.XS = g.XS;
+  ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32", "atkm_y_inv_df"), 3 * x.H1 * x.s, x.fy, op, p->fM[1], gy);
+  return cudaSuccess;
+}
+
+// x inverse (C2R) + crop
+template <typename R>
+cudaError_t atkm_pass_xi(atkm_plan* p, int, const double*, const double*, double* phi, cudaStream_t st) {
+  const AtkmCtx<R> x = atkm_ctx<R>(p);
+  const Geo& g = *x.g;
+  if (!x.W1) return cudaErrorInvalidValue;
+  const PassGrid gx = pass_grid<R>(g.Nx, true, x.nl, 0, 0);
+  OpAtkmXI<R> op; op.W1 = x.W1; op.phi = phi; op.twM = x.twM; op.c = x.c; op.XS = g.XS;
+  ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32", "atkm_x_inv_df"), x.H1 * x.s + 8 * x.N, x.fx, op, p->fN[0],
+           gx);
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t launch_atkm(atkm_plan* p, int mode, const double* a, const double* b, double* phi, cudaStream_t st) {
+  if (!ws1<R>(p) || !ws2<R>(p) || !kztab<R>(p)) return cudaErrorInvalidValue;
+  cudaError_t e = atkm_pass_xf<R>(p, mode, a, b, phi, st);
+  if (e == cudaSuccess) e = atkm_pass_yf<R>(p, mode, a, b, phi, st);
+  if (e == cudaSuccess) e = atkm_pass_z<R>(p, mode, a, b, phi, st);
+  if (e == cudaSuccess) e = atkm_pass_yi<R>(p, mode, a, b, phi, st);
+  if (e == cudaSuccess) e = atkm_pass_xi<R>(p, mode, a, b, phi, st);
+  return e;
 }
 
 // One axis pass of H_phi f (a function of its own so that heavy
