@@ -439,7 +439,8 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": it_s * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": [256, 256, 64], "step": "one PCG iteration"},
+                "config": {"workload": WORKLOAD, "grid": [256, 256, 64], "step": "one PCG iteration (all rows)",
+                           "precision": "f64"},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": "each step: one oracle PCG iteration of the workload from psi_0 "
                                            "(numpy/scipy FP64, one thread), start-up excluded",
