@@ -59,8 +59,10 @@ def parse():
     ap.add_argument("--no-precision-form", action="store_true", help="skip the FP32-bulk arm")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solve to 1e-8")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed"],
-                    help="run a small fixed amount of work on the bench grid for an ncu capture and exit")
+    ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
+                                               "profiling_overhead", "polish_df32"],
+                    help="run a small fixed amount of work on the bench grid for an ncu capture, or one of the "
+                         "timings quoted in the design notes, and exit")
     return ap.parse_args()
 
 
@@ -394,9 +396,73 @@ def run_ours(args, rank, world, local_rank):
                 launches=main["launches"], pform=pform, ttt=ttt)
 
 
+def timing_case(case: str):
+    """Timings quoted in the design notes, one JSON line each.
+    profiling_overhead: 30 FP64 PCG iterations (after 3) without and with the
+    per-pass CUDA events, twice.  polish_df32: 1500 iterations of the
+    double-word split form from psi_0 (the FP32 phase, then the polish), then
+    200 polish iterations without and with the events, with the per-pass
+    times per iteration."""
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+    w = W.CONFIGS[WORKLOAD]
+    prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
+    psi0 = torch.from_numpy(W.initial_guess(w)).cuda()
+
+    def timed(plan, psi, n, prof, kw):
+        plan.set_profiling(prof)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = plan.pcg_ground_state(prm, psi, max_iter=n, resume=True, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        stats = plan.kernel_stats() if prof else []
+        plan.set_profiling(False)
+        return r, e0.elapsed_time(e1), stats
+
+    if case == "profiling_overhead":
+        plan = B.Plan(w.N, w.L, w.n)
+        kw = dict(tol_residual=TOL, precision=B.PRECISION_F64, switch_tol=1e-5)
+        try:
+            for prof in (False, True, False, True):
+                psi = psi0.clone()
+                plan.pcg_ground_state(prm, psi, max_iter=3, **kw)
+                torch.cuda.synchronize()
+                r, ms, _ = timed(plan, psi, 30, prof, kw)
+                n = r["iters"] - 3
+                print(json.dumps({"case": case, "profiling": prof, "iters": n, "ms_per_iter": ms / max(n, 1)}))
+        finally:
+            plan.close()
+        return
+    plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
+    kw = dict(tol_residual=TOL, precision=B.PRECISION_DF32_SPLIT, switch_tol=1e-5)
+    try:
+        psi = psi0.clone()
+        r = plan.pcg_ground_state(prm, psi, max_iter=1500, **kw)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "warm_iters": r["iters"], "f32_iters": r["f32_iters"],
+                          "residual": r["residual"]}))
+        for prof in (False, True):
+            it0 = r["iters"]
+            r, ms, stats = timed(plan, psi, 200, prof, kw)
+            n = max(r["iters"] - it0, 1)
+            out = {"case": case, "profiling": prof, "iters": n, "ms_per_iter": ms / n}
+            if prof:
+                out["kernel_ms_per_iter"] = sum(k["ms_total"] for k in stats) / n
+                out["passes_ms_per_iter"] = [(k["name"], round(k["ms_total"] / n, 4))
+                                             for k in sorted(stats, key=lambda k: -k["ms_total"])]
+            print(json.dumps(out))
+    finally:
+        plan.close()
+
+
 def profile_case(case: str):
     """Small fixed workloads on the bench grid for ncu captures (about 1 GB of
     device memory): two ATKM evaluations, or three PCG iterations."""
+    if case in ("profiling_overhead", "polish_df32"):
+        timing_case(case)
+        return
     import torch
     import atkm_workloads as W
     from paper_2603_05194_gb300 import binding as B
