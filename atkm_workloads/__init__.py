@@ -192,6 +192,18 @@ CONFIGS = {
 }
 
 
+# Setups of the paper's own experiments (§3), as input recipes.
+PAPER_WORKLOADS = {
+    # Example 3.1, Case II at Omega = 0.2 (no vortex: one ground state):
+    # beta = 100, lambda = 0.8 beta, n = z, gamma = (1, 2, 10), [-16,16]^2 x [-10,10].
+    "ex31_caseII_256": Workload("ex31_caseII_256", (256, 256, 256), (16.0, 16.0, 10.0), (1.0, 2.0, 10.0),
+                                100.0, 80.0, (0.0, 0.0, 1.0), 0.2, "phi_d"),
+    # Example 3.2: U-shape vortex line in a cigar, attractive dipoles along z.
+    "ex32_256": Workload("ex32_256", (256, 256, 256), (10.0, 10.0, 100.0), (1.0, 1.0, 0.05),
+                         1000.0, -300.0, (0.0, 0.0, 1.0), 0.75, "phi_d"),
+}
+
+
 def sweep_instances(count: int = 48, seed: int = 4):
     """Uneven-grid Omega/anisotropy sweep (48 instances): Omega ~ U[0.5, 0.95],
     gamma_z in {10, 20, 40}, beta = 200, lambda/beta in {0.2, 0.4}, n = z,

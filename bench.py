@@ -11,16 +11,20 @@ start the solve from psi_0; the K timed iterations resume it (the same
 solve), bracketed by barrier + synchronize and timed with CUDA events.
 
 value = ATKM evaluations per second sustained by the full PCG step (the ATKM
-calls the K iterations made / their time); the line also carries the time per
-iteration, the stand-alone ATKM rate (FP64 and FP32), the roofline of the
-dominant kernel (timed live with CUDA events inside the timed iterations),
-an end-to-end number through the public API with host buffers, and the CPU
-oracle on a bounded sample (one oracle PCG iteration of the same workload).
-Time to 1e-8 is not a bench step here: this vortex-lattice state needs
-O(10^4) iterations to reach that residual.
+calls the K iterations made / their time).  The line also carries:
+  * roofline: the dominant pass (timed live with CUDA events inside the timed
+    iterations) against the measured HBM bandwidth or the binary64 FMA rate
+    measured in the same run, every pass's fractions, and the same for the
+    precision form (FP32 bulk) on the same iterations;
+  * e2e: the same metric through the public API with host buffers, and the
+    other half of the metric, the time to residual 1e-8: PCG-ATKM-MG
+    (Algorithm 2) from guess (d), end to end, in binary64 and in each
+    precision form, with each form's energy and mu against the binary64 result;
+  * cpu_baseline: the C++ oracle on the host's cores (all cores with OpenMP,
+    and one thread) on a bounded sample of the same workload.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision f64|mixed]
-  python bench.py --impl reference ...   # the CPU oracle on the same metric
+  python bench.py [--gpus N --steps K --warmup W] [--precision f64|mixed] [--ttt f64,f32_f64,...]
+  python bench.py --impl reference ...   # the C++ oracle on the same metric
 
 For N > 1 (torchrun) every rank runs its own replica (the solver does not
 shard; replicas only) and the value is the sum over ranks of ATKM evaluations
@@ -57,52 +61,95 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "f64"], default="f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true", help="skip the FP32-bulk arm")
-    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solve to 1e-8")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solves to 1e-8")
+    ap.add_argument("--ttt", default="f64,f32_f64,df32_split",
+                    help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
-                                               "profiling_overhead", "polish_df32"],
+                                               "profiling_overhead", "polish_df32", "fp64_peak"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture, or one of the "
                          "timings quoted in the design notes, and exit")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.no_time_to_tol:
+        a.ttt = ""
+    return a
 
 
 # --------------------------------------------------------------- CPU oracle
-def cpu_sample(iters: int = 1) -> dict:
-    """Times the CPU oracle (as it stands, one thread) on a bounded sample of
-    the workload: plan (untimed), one stand-alone ATKM evaluation, and `iters`
-    PCG iterations from psi_0 (the start-up ATKM + energy is timed separately
-    and subtracted).  Returns ATKM evaluations per second of the PCG step."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_sample(iters: int = 2) -> dict:
+    """Times the C++ oracle (plain binary64 C++17 with its own FFT, as it
+    stands) on a bounded sample of the workload, on this host's cores:
+      * single-thread: one stand-alone ATKM evaluation;
+      * all cores (OpenMP over independent FFT lines and grid planes, sums in
+        a fixed order): `iters` PCG iterations from psi_0, timed from the
+        oracle's per-iteration clock (the start-up ATKM and energy excluded).
+    Returns ATKM evaluations per second of each."""
     import numpy as np
     import atkm_workloads as W
+    import oracle.cpp_oracle as OC
     import oracle as O
     w = W.CONFIGS[WORKLOAD]
-    plan = O.Plan(w.N, w.L, w.n)
-    prm = O.Params(w.gamma, w.beta, w.lam, w.Omega)
+    cores = host_cores()
+    t0 = time.perf_counter()
+    plan = OC.Plan(w.N, w.L, w.n, threads=cores)
+    t_plan = time.perf_counter() - t0
     psi = W.initial_guess(w)
+    rho = np.abs(psi) ** 2
+    plan.set_threads(1)
     t0 = time.perf_counter()
-    plan.dipolar_potential(np.abs(psi) ** 2)
-    t_atkm = time.perf_counter() - t0
+    plan.dipolar_potential(rho)
+    t_atkm1 = time.perf_counter() - t0
+    plan.set_threads(cores)
     t0 = time.perf_counter()
-    O.pcg_ground_state(plan, prm, psi, O.PcgOptions(max_iter=0))
-    t_init = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    res = O.pcg_ground_state(plan, prm, psi, O.PcgOptions(max_iter=iters))
-    t_run = time.perf_counter() - t0
-    t_iters = max(t_run - t_init, 1e-9)
-    evals = sum(2 + e.get("halvings", 0) for e in res.log[:iters])
-    return dict(atkm_s=t_atkm, iter_s=t_iters / iters, iters=iters, evals=evals, value=evals / t_iters, threads=1)
+    plan.dipolar_potential(rho)
+    t_atkmN = time.perf_counter() - t0
+    prm = O.Params(w.gamma, w.beta, w.lam, w.Omega)
+    res = plan.pcg_ground_state(prm, psi, OC.PcgOptions(tol_residual=TOL, max_iter=iters))
+    log = res.log
+    t_iters = log[iters]["wall"] - log[0]["wall"]
+    evals = sum(2 + e.get("halvings", 0) for e in log[:iters])
+    return dict(cores=cores, plan_s=t_plan, atkm_1thread_s=t_atkm1, atkm_allcores_s=t_atkmN,
+                iters=iters, iter_s=t_iters / iters, evals=evals, value=evals / t_iters,
+                value_1thread_atkm=1.0 / t_atkm1)
 
 
 def run_cpu_sample_subprocess() -> dict:
     env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], capture_output=True, text=True,
                        env=env, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args) -> dict:
+    """The C++ oracle on the bench metric: one plan on all host cores, then one
+    run of warmup + steps PCG iterations from psi_0; each timed step is one
+    PCG iteration (from the oracle's per-iteration clock), and the value is
+    the ATKM evaluations of the timed iterations over their time."""
+    import atkm_workloads as W
+    import oracle.cpp_oracle as OC
+    import oracle as O
+    w = W.CONFIGS[WORKLOAD]
+    cores = host_cores()
+    plan = OC.Plan(w.N, w.L, w.n, threads=cores)
+    prm = O.Params(w.gamma, w.beta, w.lam, w.Omega)
+    n = args.warmup + args.steps
+    res = plan.pcg_ground_state(prm, W.initial_guess(w), OC.PcgOptions(tol_residual=TOL, max_iter=n))
+    log = res.log
+    k0, k1 = min(args.warmup, len(log) - 1), min(n, len(log) - 1)
+    sec = log[k1]["wall"] - log[k0]["wall"]
+    evals = sum(2 + e.get("halvings", 0) for e in log[k0:k1])
+    steps = k1 - k0
+    return dict(value=evals / sec, ms_per_step=sec / max(steps, 1) * 1e3, steps=steps, cores=cores, evals=evals)
 
 
 # ---------------------------------------------------------------- clocks
@@ -175,9 +222,10 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-# FP64 FMA throughput of this machine's GB300 (FMA-chain microbenchmark, 2 flops
-# per FMA, 1216 CTAs x 256 threads x 8 independent chains): 1255 GFLOP/s.
-FP64_PEAK_GFLOPS = 1255.0
+# Binary64 FMA throughput, measured in each run by the library's FMA-chain
+# kernel (atkm_measure_fp64_fma); this constant is only used when no GPU
+# measurement is available (the value measured on this machine's GB300 with it).
+FP64_PEAK_FALLBACK_GFLOPS = 1255.0
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -209,12 +257,33 @@ def aggregate_ranks(ms: float, evals: float, device: str = "cpu"):
     return float(tm.item()), float(te.item())
 
 
-def roofline(stats, peaks):
+def pass_table(stats, peaks, fp64_peak):
+    """Every pass of the timed region: CUDA-event time, algorithmic bytes and
+    flops per launch, the fraction of measured HBM bandwidth those bytes
+    reach, and (binary64 passes) the fraction of the measured FP64 FMA rate."""
+    out = []
+    for k in sorted(stats, key=lambda k: -k["ms_total"]):
+        if k["ms_total"] <= 0:
+            continue
+        gbs = k["bytes_total"] / (k["ms_total"] * 1e-3) / 1e9
+        row = {"name": k["name"], "launches": k["launches"], "ms_per_launch": round(k["ms_total"] / k["launches"], 4),
+               "GB/s": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 3)}
+        if k["flops_total"] > 0:
+            gf = k["flops_total"] / (k["ms_total"] * 1e-3) / 1e9
+            row["GFLOP/s"] = round(gf, 1)
+            if k["name"].endswith("_f64"):
+                row["fp64_frac"] = round(gf / fp64_peak["gflops"], 3)
+        out.append(row)
+    return out
+
+
+def roofline(stats, peaks, fp64_peak):
     dom = max(stats, key=lambda s: s["ms_total"]) if stats else None
     # vector kernels (FP64 vectors, HBM-bound) carry no flops: always "hbm"
     if dom is None or dom["ms_total"] <= 0:
         return None
     per_launch_ms = dom["ms_total"] / dom["launches"]
+    passes = pass_table(stats, peaks, fp64_peak)
     if dom["name"].endswith("_f32") or dom["name"].startswith("vec_"):
         achieved = dom["bytes_total"] / (dom["ms_total"] * 1e-3) / 1e9
         return {"kernel": dom["name"], "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
@@ -223,17 +292,27 @@ def roofline(stats, peaks):
                 "traffic": NCU_TRAFFIC.get(dom["name"], {}).get("bytes"),
                 "traffic_source": NCU_TRAFFIC.get(dom["name"], {}).get("profile"),
                 "algorithmic_bytes_per_launch": dom["bytes_total"] / dom["launches"],
-                "launch_ms": round(per_launch_ms, 4), "launches": dom["launches"]}
+                "launch_ms": round(per_launch_ms, 4), "launches": dom["launches"], "passes": passes}
     achieved = dom["flops_total"] / (dom["ms_total"] * 1e-3) / 1e9
-    return {"kernel": dom["name"], "bound": "alu", "achieved": round(achieved, 1), "peak": FP64_PEAK_GFLOPS,
-            "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-            "peak_source": "measured FP64 FMA microbenchmark on this pool's GB300",
+    return {"kernel": dom["name"], "bound": "alu", "achieved": round(achieved, 1), "peak": round(fp64_peak["gflops"], 1),
+            "unit": "GFLOP/s", "frac": round(achieved / fp64_peak["gflops"], 4),
+            "peak_source": fp64_peak["source"],
             "traffic": NCU_TRAFFIC.get(dom["name"], {}).get("bytes"),
             "traffic_source": NCU_TRAFFIC.get(dom["name"], {}).get("profile"),
             "algorithmic_flops_per_launch": dom["flops_total"] / dom["launches"],
             "algorithmic_bytes_per_launch": dom["bytes_total"] / dom["launches"],
             "hbm_GBs": round(dom["bytes_total"] / (dom["ms_total"] * 1e-3) / 1e9, 1),
-            "launch_ms": round(per_launch_ms, 4), "launches": dom["launches"]}
+            "launch_ms": round(per_launch_ms, 4), "launches": dom["launches"], "passes": passes}
+
+
+def fp64_peak_now(B) -> dict:
+    """The binary64 FMA rate of this GPU, measured now (best of 5 launches)."""
+    try:
+        g = B.measure_fp64_fma()
+        return {"gflops": g, "source": "measured in this run: atkm_measure_fp64_fma (FMA chains, 8 CTAs/SM x 256 "
+                                       "threads x 8 chains, best of 5)"}
+    except Exception as exc:  # reported, not fatal
+        return {"gflops": FP64_PEAK_FALLBACK_GFLOPS, "source": f"fallback constant (measurement failed: {exc})"[:200]}
 
 
 def timed_steps(B, plan, prm, psi0, precision, warmup, steps, barrier, clk=None):
@@ -274,40 +353,88 @@ def rel2(a, b) -> float:
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
-def time_to_tol(B, w):
-    """PCG-ATKM-MG (Algorithm 2; levels N/4, N/2, N) in the double-word split
-    form from guess (d) on the coarsest grid to residual 1e-8 (residual formed
-    from the double-word H phi, about 1e-14 relative), wall time around the
-    call; plus the FP32- and double-word-vs-FP64 ATKM errors at the final
-    state."""
+TTT_FORMS = {
+    "f64": ("PRECISION_F64", "every operator, reduction and step in binary64 (the paper's precision)"),
+    "f32_f64": ("PRECISION_F32_F64", "FP32 FFT/ATKM/H/P (binary64 reductions, retraction and renormalisation) "
+                                     "until residual 1e-5, then a binary64 polish"),
+    "f32_split": ("PRECISION_F32_SPLIT", "FP32 bulk; binary64 polish of H phi, the trial-energy ATKM, the "
+                                         "reductions and the retraction, with P r, H p and the step-model ATKM "
+                                         "in FP32"),
+    "df32_split": ("PRECISION_DF32_SPLIT", "FP32 bulk; polish as f32_split with H phi and the trial-energy ATKM "
+                                           "in double-FP32 (about 48-bit) arithmetic"),
+}
+
+
+def time_to_tol(B, w, forms):
+    """Time to residual 1e-8 through the public API, end to end: psi_0 (guess
+    (d) on the coarsest grid) copied from pinned host memory, PCG-ATKM-MG
+    (Algorithm 2; levels N/4, N/2, N) to ||H phi - mu phi|| <= 1e-8, the
+    final state copied back; wall time around all of it.  One solve per
+    precision form, each compared with the binary64 solve (relative E and mu
+    differences, and Phi of the final state in FP32 and double-word against
+    binary64)."""
     import torch
     import atkm_workloads as W
     from paper_2603_05194_gb300 import multigrid as MG
-
-    def guess(p, N):
-        return W.initial_guess(W.with_grid(p, N))
-
-    res, sec, psi, grids = MG.solve_mg(w, guess, levels=3, tol=TOL, max_iter=20000,
-                                       precision=B.PRECISION_DF32_SPLIT)
-    plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
-    try:
-        phi64 = plan.dipolar_potential_from_psi(psi)
-        phi32 = plan.dipolar_potential_from_psi(psi, f32=True)
-        phidw = plan.dipolar_potential_from_psi(psi, df32=True)
-        prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
-        e64 = plan.energy_parts(prm, psi, phi64)
-        e32 = plan.energy_parts(prm, psi, phi32)
-        err = {"Phi_rel_l2_f32_vs_f64": rel2(phi32, phi64), "Phi_rel_l2_df32_vs_f64": rel2(phidw, phi64),
-               "E_rel_f32_vs_f64": abs(e32["E"] - e64["E"]) / abs(e64["E"]),
-               "mu_rel_f32_vs_f64": abs(e32["mu"] - e64["mu"]) / abs(e64["mu"])}
-    finally:
-        plan.close()
-    out = MG.summary(res, sec, grids)
-    out.update(method="PCG-ATKM-MG, 3 levels, double-word split form (FP32 bulk; polish with H phi and the "
-                      "trial-energy ATKM in double-FP32, reductions and retraction in FP64, P r / H p / "
-                      "step-model ATKM in FP32)", tol=TOL,
-               precision_errors_at_final_state=err)
+    grids = MG.level_grids(w.N, 3)
+    psi0_host = torch.from_numpy(W.initial_guess(W.with_grid(w, grids[0]))).pin_memory()
+    out = {"workload": w.name, "tol": TOL,
+           "method": "PCG-ATKM-MG (Algorithm 2), 3 levels from guess (d) on the coarsest grid",
+           "grids": [list(g) for g in grids], "forms": {}}
+    finals = {}
+    for name in forms:
+        prec = getattr(B, TTT_FORMS[name][0])
+        f32 = prec != B.PRECISION_F64
+        plans = [B.Plan(N, w.L, w.n, f32=f32, df32=prec == B.PRECISION_DF32_SPLIT) for N in grids]
+        try:
+            psis = [torch.empty(p.shape, dtype=torch.complex128, device="cuda") for p in plans]
+            host_out = torch.empty(plans[-1].shape, dtype=torch.complex128).pin_memory()
+            prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            psis[0].copy_(psi0_host, non_blocking=True)
+            res = B.pcg_ground_state_mg(plans, prm, psis, tol_residual=TOL, max_iter=20000, precision=prec)
+            host_out.copy_(psis[-1], non_blocking=True)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+        finally:
+            for p in plans:
+                p.close()
+        finals[name] = host_out
+        out["forms"][name] = {"seconds": round(sec, 3), "status": res[-1]["status_name"], "E": res[-1]["E"],
+                              "mu": res[-1]["mu"], "residual": res[-1]["residual"],
+                              "iters": [r["iters"] for r in res], "f32_iters": [r["f32_iters"] for r in res],
+                              "arithmetic": TTT_FORMS[name][1]}
+    if "f64" in out["forms"]:
+        ref = out["forms"]["f64"]
+        for name, d in out["forms"].items():
+            d["E_rel_vs_f64"] = abs(d["E"] - ref["E"]) / abs(ref["E"])
+            d["mu_rel_vs_f64"] = abs(d["mu"] - ref["mu"]) / abs(ref["mu"])
+            d["speedup_vs_f64"] = round(ref["seconds"] / d["seconds"], 3)
+        # FP32 and double-word ATKM against binary64 at the binary64 ground state
+        plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
+        try:
+            psi = finals["f64"].cuda()
+            phi64 = plan.dipolar_potential_from_psi(psi)
+            phi32 = plan.dipolar_potential_from_psi(psi, f32=True)
+            phidw = plan.dipolar_potential_from_psi(psi, df32=True)
+            prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
+            e64, e32 = plan.energy_parts(prm, psi, phi64), plan.energy_parts(prm, psi, phi32)
+            out["errors_at_f64_ground_state"] = {
+                "Phi_rel_l2_f32": rel2(phi32, phi64), "Phi_rel_l2_df32": rel2(phidw, phi64),
+                "E_rel_f32_Phi": abs(e32["E"] - e64["E"]) / abs(e64["E"]),
+                "mu_rel_f32_Phi": abs(e32["mu"] - e64["mu"]) / abs(e64["mu"])}
+        finally:
+            plan.close()
     return out
+
+
+def bench_config(precision: str, world: int) -> dict:
+    """The workload, identical in both arms of the benchmark."""
+    return {"workload": WORKLOAD, "grid": [256, 256, 64], "box": [16.0, 16.0, 1.5],
+            "step": "one PCG iteration of Algorithm 1 (all hot-path rows)", "precision": precision,
+            "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (padded ATKM spectrum 268-537 MB per pass)"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -321,6 +448,8 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as td
     w = W.CONFIGS[WORKLOAD]
     precision = B.PRECISION_F32_F64 if args.precision == "mixed" else B.PRECISION_F64
+    fp64_peak = fp64_peak_now(B)
+    peaks = measured_peaks()
     plan = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
     prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
     psi0_host = torch.from_numpy(W.initial_guess(w)).pin_memory()
@@ -344,11 +473,11 @@ def run_ours(args, rank, world, local_rank):
         mms, mev = aggregate_ranks(mx["ms"], float(mx["evals"]), "cuda") if dist else (mx["ms"], float(mx["evals"]))
         pform = {"value": round(mev / (mms * 1e-3), 2), "unit": UNIT,
                  "ms_per_step": round(mms / max(mx["steps"], 1), 3), "steps": mx["steps"],
-                 "roofline": roofline(mx["stats"], measured_peaks()), "kernels": kernel_table(mx["stats"]),
+                 "roofline": roofline(mx["stats"], peaks, fp64_peak),
                  "gpu_launches": mx["launches"], "residual_after_steps": mx["res"]["residual"],
                  "f32_iterations": mx["res"]["f32_iters"]}
 
-    # ---- stand-alone ATKM evaluations per second (FP64 and FP32 arithmetic)
+    # ---- stand-alone ATKM evaluations per second (FP64, double-word, FP32)
     Phi = torch.empty(w.shape, dtype=torch.float64, device="cuda")
     standalone = {}
     for key, kw in (("f64", {}), ("df32", {"df32": True}), ("f32", {"f32": True})):
@@ -387,13 +516,17 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- time to the residual tolerance (single process only: replicas would
     # only repeat it)
-    ttt = None
-    if not args.no_time_to_tol and world == 1:
-        ttt = time_to_tol(B, w)
+    ttt = ttt_u = None
+    forms = [f for f in args.ttt.split(",") if f] if args.ttt else []
+    if forms and world == 1:
+        ttt = time_to_tol(B, w, forms)
+        # the same on a workload with one ground state (no vortex), where every
+        # form must end at the binary64 energy: Example 3.1, Case II, Omega = 0.2
+        ttt_u = time_to_tol(B, W.PAPER_WORKLOADS["ex31_caseII_256"], forms)
     return dict(ms=ms_max, evals=evals_all, steps=main["steps"], res=main["res"], standalone=standalone,
                 e2e_value=e2e_evals * world / (e2e_ms * 1e-3), nbytes=nbytes,
-                roof=roofline(main["stats"], measured_peaks()), stats=main["stats"], clocks=main["clocks"],
-                launches=main["launches"], pform=pform, ttt=ttt)
+                roof=roofline(main["stats"], peaks, fp64_peak), stats=main["stats"], clocks=main["clocks"],
+                launches=main["launches"], pform=pform, ttt=ttt, ttt_u=ttt_u, fp64_peak=fp64_peak)
 
 
 def timing_case(case: str):
@@ -459,9 +592,17 @@ def timing_case(case: str):
 
 def profile_case(case: str):
     """Small fixed workloads on the bench grid for ncu captures (about 1 GB of
-    device memory): two ATKM evaluations, or three PCG iterations."""
+    device memory): two ATKM evaluations, or three PCG iterations; or a
+    timing quoted in the design notes; or the binary64 FMA peak (fp64_peak:
+    the roofline denominator of the binary64 passes, one JSON line)."""
     if case in ("profiling_overhead", "polish_df32"):
         timing_case(case)
+        return
+    if case == "fp64_peak":
+        from paper_2603_05194_gb300 import binding as B
+        runs = [B.measure_fp64_fma(blocks_per_sm=b, iters=4096, repeats=5) for b in (4, 8, 16)]
+        print(json.dumps({"case": case, "gflops_by_blocks_per_sm": {"4": runs[0], "8": runs[1], "16": runs[2]},
+                          "gflops": max(runs)}))
         return
     import torch
     import atkm_workloads as W
@@ -495,22 +636,20 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        # The CPU oracle on the same metric, rank 0 only; other ranks exit without work.
+        # The C++ oracle on the same metric, rank 0 only; other ranks exit without work.
         if rank != 0:
             return
-        samples = [run_cpu_sample_subprocess() for _ in range(args.warmup + args.steps)]
-        timed = samples[args.warmup:] if len(samples) > args.warmup else samples
-        value = statistics.median(s["value"] for s in timed)
-        it_s = statistics.median(s["iter_s"] for s in timed)
+        r = reference_arm(args)
+        value = r["value"]
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": it_s * 1e3, "higher_is_better": True,
+                "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": [256, 256, 64], "step": "one PCG iteration (all rows)",
-                           "precision": "f64"},
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": "each step: one oracle PCG iteration of the workload from psi_0 "
-                                           "(numpy/scipy FP64, one thread), start-up excluded",
-                                 "standalone_atkm_evals_per_s": 1.0 / statistics.median(s["atkm_s"] for s in timed)},
+                "config": bench_config(args.precision, args.gpus),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                 "sample": f"the C++ oracle (plain C++17 binary64, own mixed-radix FFT, OpenMP over "
+                                           f"FFT lines and grid planes, fixed-order sums) on {r['cores']} host cores: "
+                                           f"one run of warmup + steps PCG iterations from psi_0, each step one "
+                                           f"iteration ({r['evals']} ATKM evaluations in the timed steps)"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -524,38 +663,43 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             s = run_cpu_sample_subprocess()
-            cpu = {"value": round(s["value"], 4), "unit": UNIT, "cores": s["threads"], "kind": "oracle",
-                   "sample": f"one oracle PCG iteration of the same workload from psi_0 ({s['iter_s']:.1f} s, "
-                             f"{s['evals']} ATKM evals; numpy/scipy FP64, one thread); stand-alone oracle ATKM "
-                             f"{s['atkm_s']:.2f} s"}
+            cpu = {"value": round(s["value"], 4), "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                   "sample": f"the C++ oracle (plain C++17 binary64 with its own FFT) on the same workload, all "
+                             f"{s['cores']} host cores (OpenMP, fixed-order sums): {s['iters']} PCG iterations from "
+                             f"psi_0 ({s['iter_s']:.2f} s each, {s['evals']} ATKM evaluations); plan "
+                             f"{s['plan_s']:.1f} s untimed",
+                   "single_thread": {"atkm_evals_per_s": round(s["value_1thread_atkm"], 4), "cores": 1,
+                                     "sample": f"one stand-alone ATKM evaluation, one thread "
+                                               f"({s['atkm_1thread_s']:.2f} s)"},
+                   "allcores_standalone_atkm_s": round(s["atkm_allcores_s"], 3)}
         except Exception as exc:  # reported, not fatal
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"[:300]}
+            cpu = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                   "sample": f"failed: {exc}"[:300]}
     if rank == 0:
         res = out["res"]
         value = out["evals"] / (out["ms"] * 1e-3)
-        ktable = kernel_table(out["stats"], 24)
+        roof = out["roof"]
+        if roof is not None and out["pform"] is not None:
+            roof["precision_form"] = out["pform"]
+        e2e = {"value": round(out["e2e_value"], 2), "unit": UNIT,
+               "h2d_bytes_per_step": round(out["nbytes"] / (args.warmup + args.steps)),
+               "d2h_bytes_per_step": round(out["nbytes"] / (args.warmup + args.steps)),
+               "note": "pcg_ground_state from pinned host psi_0: one H2D of psi_0, warmup+steps iterations, one D2H "
+                       "of the state, all inside the timed region (bytes per step = bytes / iterations)"}
+        if out["ttt"] is not None:
+            e2e["time_to_1e-8"] = out["ttt"]
+            e2e["time_to_1e-8_one_ground_state"] = out["ttt_u"]
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": out["steps"],
             "warmup": args.warmup, "ms_per_step": round(out["ms"] / max(out["steps"], 1), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "f64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [256, 256, 64], "step": "one PCG iteration (all rows)",
-                       "precision": args.precision, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (padded ATKM spectrum 268-537 MB per pass)",
-                       "atkm_evals_in_steps": int(out["evals"]), "iteration_after_steps": res["iters"],
-                       "residual_after_steps": res["residual"], "E_after_steps": res["E"],
-                       "halvings": res["halvings"]},
-            "standalone_atkm_evals_per_s": out["standalone"],
-            "roofline": out["roof"], "kernels": ktable, "clocks": out["clocks"],
-            "gpu_launches": out["launches"],
-            "e2e": {"value": round(out["e2e_value"], 2), "unit": UNIT,
-                    "h2d_bytes_per_step": round(out["nbytes"] / (args.warmup + args.steps)),
-                    "d2h_bytes_per_step": round(out["nbytes"] / (args.warmup + args.steps)),
-                    "note": "pcg_ground_state from pinned host psi_0: one H2D of psi_0, warmup+steps iterations, "
-                            "one D2H of the state, all inside the timed region (bytes per step = bytes / iterations)"},
+            "config": bench_config(args.precision, world),
+            "roofline": roof, "clocks": out["clocks"], "gpu_launches": out["launches"], "e2e": e2e,
             "cpu_baseline": cpu,
-            "precision_form": out["pform"],
-            "time_to_1e-8": out["ttt"],
+            "run": {"atkm_evals_in_steps": int(out["evals"]), "iteration_after_steps": res["iters"],
+                    "residual_after_steps": res["residual"], "E_after_steps": res["E"], "halvings": res["halvings"],
+                    "standalone_atkm_evals_per_s": out["standalone"], "fp64_fma_peak": out["fp64_peak"]},
         }
         print(json.dumps(line))
     if dist:

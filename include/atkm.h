@@ -43,7 +43,7 @@ typedef enum atkm_status {
   ATKM_NOT_CONVERGED = 5,        /* PCG reached max_iter before the stop rule     */
   ATKM_STAGNATED = 6,            /* three consecutive exhausted halving loops     */
   ATKM_ERR_NAN = 7,              /* a NaN/Inf appeared in the PCG scalars         */
-  ATKM_ERR_TIMEOUT = 8           /* reserved: a bounded device wait ran out       */
+  ATKM_ERR_TIMEOUT = 8           /* the solve reached opts.time_limit_s           */
 } atkm_status;
 
 typedef struct atkm_plan atkm_plan;
@@ -105,6 +105,18 @@ typedef struct atkm_kernel_stat {
 /* Number of CUDA kernels this library has launched in this process (all
  * plans, all calls); the difference around a region counts its launches. */
 unsigned long long atkm_launch_count(void);
+
+/*
+ * atkm_measure_fp64_fma -- peak binary64 FMA rate of the current device, the
+ * denominator of the roofline of the binary64 FFT passes (bound by that
+ * pipe on this GPU).  Launches blocks_per_sm x (SM count) CTAs of 256
+ * threads, each thread running 8 independent FMA chains of `iters` steps;
+ * times `repeats` launches (after one warm-up) with CUDA events on `stream`
+ * and writes the best rate in GFLOP/s (2 flops per FMA) to *gflops (host).
+ * Allocates and frees a small output buffer; synchronises the stream.
+ * Measurement support; the paper has no counterpart.
+ */
+int atkm_measure_fp64_fma(int blocks_per_sm, int iters, int repeats, double* gflops, void* stream);
 
 /* on != 0 clears the record and starts recording; on == 0 stops. */
 int atkm_plan_set_profiling(atkm_plan* plan, int on);
@@ -205,8 +217,8 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
 /* Precision modes of the PCG driver. */
 #define ATKM_PRECISION_F64 0      /* every step in FP64                          */
 #define ATKM_PRECISION_F32_F64 1  /* complex64 FFT/ATKM/H/P until switch_tol, two exhausted
-                                     halving loops, or 400 iterations without halving the
-                                     best FP32 residual; then FP64                     */
+                                     halving loops, or f32_window iterations without
+                                     halving the best FP32 residual; then FP64          */
 #define ATKM_PRECISION_F32_SPLIT 2 /* as ATKM_PRECISION_F32_F64, and after the hand-over the
                                      operators that only shape the search direction and
                                      the step-size model (P r, H p and the ATKM of
@@ -235,6 +247,13 @@ typedef struct atkm_pcg_opts {
                            the iterations of this call                              */
   int no_graphs;        /* != 0: launch every kernel directly instead of replaying the
                            captured CUDA graph of an iteration (same results)       */
+  double time_limit_s;  /* if > 0: stop with ATKM_ERR_TIMEOUT once this many seconds
+                           of wall-clock time have passed since the call began,
+                           checked at the top of every iteration (on the device,
+                           from its global timer, in the device-driven loop); the
+                           state reached is returned and can be resumed          */
+  int f32_window;       /* precision forms: FP32-phase iterations without halving the
+                           best FP32 residual before the hand-over (0: 400)      */
 } atkm_pcg_opts;
 
 /* One record per iteration n (values at phi_n; step fields describe n -> n+1). */
@@ -249,6 +268,8 @@ typedef struct atkm_result {
   int iters, halvings, f32_iters, status;
   atkm_iter_log* log;   /* host array of opts.log_capacity entries (may be NULL) */
   int log_count;        /* entries written                                       */
+  int device_loop;      /* 1 when the device-driven graph ran the iterations, 0 when
+                           the host took the decisions between them              */
 } atkm_result;
 
 /*
@@ -258,13 +279,19 @@ typedef struct atkm_result {
  *   psi_inout  N complex: initial guess in, final state out (normalised on entry).
  *   out        host struct; out->log (host) receives per-iteration records.
  * Allocates the PCG vectors, a plan-owned stream and graph state on first use
- * (kept by the plan).  The step decisions run in control kernels on the
- * device; each iteration is a fixed kernel sequence captured once as a CUDA
- * graph and replayed on the plan's stream, which is ordered after `stream`'s
- * prior work on entry and before its later work on return.  The host
- * synchronises once per iteration (stop rule, log) and once per halving.
- * Returns ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN or an
- * argument/CUDA error; out->status holds the same value.
+ * (kept by the plan).  Every decision runs in control kernels on the device:
+ * the solve (the FP32 phase, the hand-over and the polish of the precision
+ * forms included) is one CUDA graph whose conditional nodes loop over the
+ * iterations and the halvings, built once per plan and form and launched once
+ * on the plan's stream, which is ordered after `stream`'s prior work on entry
+ * and before its later work on return; the host synchronises once at the
+ * start (the check of psi_0) and once at the end.  Every graph loop is bounded
+ * by a count derived from max_iter and max_halvings.  While per-pass profiling
+ * is on, or with no_graphs, the host takes the same decisions between
+ * iterations instead (one synchronisation per iteration and per halving);
+ * the results are identical.
+ * Returns ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN,
+ * ATKM_ERR_TIMEOUT or an argument/CUDA error; out->status holds the same value.
  */
 int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opts* opts,
                      double* psi_inout, atkm_result* out, void* stream);
@@ -273,11 +300,13 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
  * pcg_ground_state_batched -- `count` independent solves of Algorithm 1 (an
  * Omega or anisotropy sweep) on one GPU.  Grids may differ: instance i uses
  * plans[i] (each instance needs its own plan), prm[i], psi[i] (device, in/out)
- * and out[i] (its log pointer is honoured); all share `opts`.  Every instance
- * replays its captured iteration graph on its own plan stream, so instances
- * run concurrently on the GPU; the host polls the streams and processes and
- * relaunches each instance as soon as its last phase has finished (small
- * grids do not wait for large ones).  Results are bitwise identical to
+ * and out[i] (its log pointer is honoured); all share `opts`.  The solves of
+ * all instances are built into one CUDA graph (one independent chain of
+ * conditional loops per instance) and launched once: the instances run
+ * concurrently on the GPU and each ends on its own stop rule, with no host
+ * work until all have ended.  (With profiling on or graphs off, the host
+ * instead polls the instances' streams and relaunches each as soon as its
+ * last phase has finished.)  Results are bitwise identical to
  * pcg_ground_state on each instance alone.  Returns
  * ATKM_OK if every instance converged, else the first non-OK status
  * (ATKM_ERR_CUDA takes precedence); per-instance statuses are in out[i].status.
@@ -346,6 +375,13 @@ int atkm_guess_net_grad(atkm_guess_net* net, int batch, const float* feats, cons
                         float* grad_out, float* loss, void* stream);
 int atkm_guess_net_train_step(atkm_guess_net* net, int batch, const float* feats, const double* targets,
                               float lr, float* loss, void* stream);
+/* One training step as atkm_guess_net_train_step, with every GEMM bracketed by
+ * CUDA events on `stream`: *gemm_ms = their summed time, *step_ms = the whole
+ * step, *gemm_calls = the GEMMs timed (host outputs; synchronises `stream`).
+ * Measurement support; the paper has no counterpart. */
+int atkm_guess_net_profile_step(atkm_guess_net* net, int batch, const float* feats, const double* targets,
+                                float lr, float* loss, double* gemm_ms, double* step_ms, int* gemm_calls,
+                                void* stream);
 
 /*
  * atkm_inner_products_noalloc -- out[i] = hvol * Re(sum_j u_i[j] conj(v_i[j]))

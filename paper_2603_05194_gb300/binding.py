@@ -50,7 +50,8 @@ class Energy(C.Structure):
 class PcgOpts(C.Structure):
     _fields_ = [("tol_residual", C.c_double), ("tol_linf", C.c_double), ("max_iter", C.c_int),
                 ("max_halvings", C.c_int), ("precision_mode", C.c_int), ("switch_tol", C.c_double),
-                ("log_capacity", C.c_int), ("resume", C.c_int), ("no_graphs", C.c_int)]
+                ("log_capacity", C.c_int), ("resume", C.c_int), ("no_graphs", C.c_int), ("time_limit_s", C.c_double),
+                ("f32_window", C.c_int)]
 
 
 class IterLog(C.Structure):
@@ -69,7 +70,7 @@ class Result(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("E", "mu", "E_kin", "E_pot", "E_int", "E_dip", "E_rot", "virial",
                                           "residual", "linf_step")] + \
                [("iters", C.c_int), ("halvings", C.c_int), ("f32_iters", C.c_int), ("status", C.c_int),
-                ("log", C.POINTER(IterLog)), ("log_count", C.c_int)]
+                ("log", C.POINTER(IterLog)), ("log_count", C.c_int), ("device_loop", C.c_int)]
 
 
 _lib = None
@@ -113,7 +114,9 @@ def load_library(path: str = LIB_PATH):
         "atkm_guess_net_forward": (ip, [vp, C.c_int, vp, vp, vp]),
         "atkm_guess_net_grad": (ip, [vp, C.c_int, vp, vp, vp, vp, vp]),
         "atkm_guess_net_train_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, vp]),
+        "atkm_guess_net_profile_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, dp, dp, C.POINTER(C.c_int), vp]),
         "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
+        "atkm_measure_fp64_fma": (ip, [C.c_int, C.c_int, C.c_int, dp, vp]),
         "atkm_launch_count": (C.c_ulonglong, []),
         "atkm_inner_products_noalloc": (ip, [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_ulonglong, C.c_double, vp,
                                              vp]),
@@ -128,7 +131,8 @@ def load_library(path: str = LIB_PATH):
 
 
 def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, max_iter=10000, max_halvings=20,
-                             precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True) -> list:
+                             precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True,
+                             time_limit_s=0.0, f32_window=0) -> list:
     """Runs independent solves (one plan each, grids may differ) concurrently
     through pcg_ground_state_batched; returns one result dict per instance."""
     lib = load_library()
@@ -137,13 +141,14 @@ def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.
         raise ValueError("plans, params and psis must have the same, non-zero length")
     for pl, ps in zip(plans, psis):
         _ptr(ps, torch.complex128, pl.shape, "psi")
-    opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1)
+    opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1,
+                   time_limit_s, f32_window)
     ph = (C.c_void_p * n)(*[pl._h for pl in plans])
     pa = (Params * n)(*params)
     pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
     res = (Result * n)()
     code = lib.pcg_ground_state_batched(n, ph, pa, C.byref(opts), pp, res, _stream(stream))
-    if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN):
+    if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN, ATKM_ERR_TIMEOUT):
         raise AtkmError(code, lib.atkm_last_error_string(None).decode())
     outs = []
     for i in range(n):
@@ -154,7 +159,8 @@ def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.
 
 
 def pcg_ground_state_mg(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, max_iter=10000, max_halvings=20,
-                        precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True) -> list:
+                        precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True, time_limit_s=0.0,
+                        f32_window=0) -> list:
     """Cascadic multigrid PCG-ATKM-MG through pcg_ground_state_mg: plans and
     psis from the coarsest level to the finest, psis[0] the initial guess.
     Returns one result dict per level."""
@@ -164,12 +170,13 @@ def pcg_ground_state_mg(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, ma
         raise ValueError("plans and psis must have the same, non-zero length")
     for pl, ps in zip(plans, psis):
         _ptr(ps, torch.complex128, pl.shape, "psi")
-    opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1)
+    opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1,
+                   time_limit_s, f32_window)
     ph = (C.c_void_p * n)(*[pl._h for pl in plans])
     pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
     res = (Result * n)()
     code = lib.pcg_ground_state_mg(n, ph, C.byref(params), C.byref(opts), pp, res, _stream(stream))
-    if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN):
+    if code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_NAN, ATKM_ERR_TIMEOUT):
         raise AtkmError(code, lib.atkm_last_error_string(None).decode())
     outs = []
     for i in range(n):
@@ -276,6 +283,29 @@ class GuessNet:
                                                         C.c_void_p(targets.data_ptr()), C.c_float(lr),
                                                         C.c_void_p(loss.data_ptr()), _stream(stream)))
         return loss
+
+    def profile_step(self, feats: torch.Tensor, targets: torch.Tensor, lr: float, stream=None) -> dict:
+        """One training step with its GEMMs timed by CUDA events (see include/atkm.h)."""
+        B = feats.shape[0]
+        _ptr(feats, torch.float32, (B, 8), "feats")
+        _ptr(targets, torch.complex128, (B,) + GUESS_SHAPE, "targets")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        g, t, n = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
+        self._check(self._lib.atkm_guess_net_profile_step(self._h, B, C.c_void_p(feats.data_ptr()),
+                                                          C.c_void_p(targets.data_ptr()), C.c_float(lr),
+                                                          C.c_void_p(loss.data_ptr()), C.byref(g), C.byref(t),
+                                                          C.byref(n), _stream(stream)))
+        return {"gemm_ms": g.value, "step_ms": t.value, "gemm_calls": n.value, "loss": float(loss.item())}
+
+
+def measure_fp64_fma(blocks_per_sm=8, iters=4096, repeats=5, stream=None) -> float:
+    """Peak binary64 FMA rate of the current device in GFLOP/s (see include/atkm.h)."""
+    lib = load_library()
+    g = C.c_double(0.0)
+    code = lib.atkm_measure_fp64_fma(blocks_per_sm, iters, repeats, C.byref(g), _stream(stream))
+    if code != ATKM_OK:
+        raise AtkmError(code, lib.atkm_last_error_string(None).decode())
+    return g.value
 
 
 def launch_count() -> int:
@@ -418,16 +448,17 @@ class Plan:
     # ---- Algorithm 1
     def pcg_ground_state(self, prm: Params, psi, tol_residual=1e-8, tol_linf=0.0, max_iter=10000,
                          max_halvings=20, precision=PRECISION_F64, switch_tol=1e-5, log_capacity=0,
-                         stream=None, check=True, resume=False, graphs=True) -> dict:
+                         stream=None, check=True, resume=False, graphs=True, time_limit_s=0.0,
+                         f32_window=0) -> dict:
         opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, log_capacity,
-                       1 if resume else 0, 0 if graphs else 1)
+                       1 if resume else 0, 0 if graphs else 1, time_limit_s, f32_window)
         res = Result()
         logs = (IterLog * max(1, log_capacity))()
         res.log = C.cast(logs, C.POINTER(IterLog)) if log_capacity > 0 else C.POINTER(IterLog)()
         code = self._lib.pcg_ground_state(self._h, C.byref(prm), C.byref(opts),
                                           _ptr(psi, torch.complex128, self.shape, "psi"), C.byref(res),
                                           _stream(stream))
-        if check and code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED):
+        if check and code not in (ATKM_OK, ATKM_NOT_CONVERGED, ATKM_STAGNATED, ATKM_ERR_TIMEOUT):
             self._check(code)
         out = {k: getattr(res, k) for k, _ in Result._fields_ if k != "log"}
         out["status_name"] = STATUS_NAMES.get(res.status, str(res.status))

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -97,6 +98,25 @@ template <typename R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
 // s * i * a  (s = +1 or -1)
 template <typename R, int S> __device__ __forceinline__ cx<R> mul_si(cx<R> a) {
   return S > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+
+// Number of SMs of the current device, queried once per device ordinal and
+// cached; 0 when the query fails (callers then size their grids without it).
+inline int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 0;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 0;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 // ------------------------------------------------------------- FFT engine

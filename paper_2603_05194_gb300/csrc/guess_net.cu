@@ -369,12 +369,40 @@ cudaError_t net_ensure(atkm_guess_net* n, int B) {
 }
 
 // C (+)= A(M x K) B(K x N) with the given strides; zeroes C first when split.
+// While set (atkm_guess_net_profile_step), every GEMM is bracketed by CUDA
+// events recorded on its stream (the zeroing of split-K outputs included).
+struct GemmTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+};
+thread_local GemmTimer* g_gemm_timer = nullptr;
+
+cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc,
+                        int M, int N, int K, cudaStream_t st, bool split_k);
+
 cudaError_t gemm(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc, int M, int N,
                  int K, cudaStream_t st, bool split_k) {
+  if (!g_gemm_timer) return gemm_launch(A, sam, sak, Bm, sbk, sbn, C, ldc, M, N, K, st, split_k);
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  if (e == cudaSuccess) e = gemm_launch(A, sam, sak, Bm, sbk, sbn, C, ldc, M, N, K, st, split_k);
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (a && b) g_gemm_timer->ev.emplace_back(a, b);
+  else {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  return e;
+}
+
+cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc,
+                        int M, int N, int K, cudaStream_t st, bool split_k) {
   int splits = 1;
   const int tiles = ((M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
-  if (split_k && tiles < 152) {
-    splits = (152 * 4) / tiles;
+  const int nsm = std::max(device_sm_count(), 1);
+  if (split_k && tiles < nsm) {
+    splits = (nsm * 4) / tiles;
     const int maxs = (K + kTK - 1) / kTK;
     if (splits > maxs) splits = maxs;
     if (splits < 1) splits = 1;
@@ -555,6 +583,45 @@ int atkm_guess_net_train_step(atkm_guess_net* n, int batch, const float* feats, 
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_train_step");
+}
+
+/* One training step (as atkm_guess_net_train_step) with its GEMMs timed by
+ * CUDA events: *gemm_ms the summed GEMM time, *step_ms the whole step, both
+ * on `stream`, which this call synchronises. */
+int atkm_guess_net_profile_step(atkm_guess_net* n, int batch, const float* feats, const double* targets, float lr,
+                                float* loss, double* gemm_ms, double* step_ms, int* gemm_calls, void* stream) {
+  if (!gemm_ms || !step_ms || !gemm_calls) return net_fail(n, ATKM_ERR_ARG, "atkm_guess_net_profile_step: NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  GemmTimer timer;
+  int code = ATKM_OK;
+  if (e == cudaSuccess) {
+    g_gemm_timer = &timer;
+    code = atkm_guess_net_train_step(n, batch, feats, targets, lr, loss, stream);
+    g_gemm_timer = nullptr;
+    e = cudaEventRecord(e1, st);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  double g = 0.0;
+  float ms = 0.0f;
+  for (auto& pr : timer.ev) {
+    float t = 0.0f;
+    if (e == cudaSuccess && cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) g += t;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (code != ATKM_OK) return code;
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "atkm_guess_net_profile_step");
+  *gemm_ms = g;
+  *step_ms = ms;
+  *gemm_calls = (int)timer.ev.size();
+  return ATKM_OK;
 }
 
 }  // extern "C"

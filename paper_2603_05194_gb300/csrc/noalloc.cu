@@ -15,7 +15,7 @@ namespace atkm {
 namespace {
 
 constexpr int kNaPairs = ATKM_NOALLOC_MAX_PAIRS;  // pairs per call
-constexpr int kNaBlocks = 1216;                    // reduction CTAs (8 per SM on 152 SMs)
+constexpr int kNaBlocks = 1216;                    // most reduction CTAs of a call (scratch capacity)
 constexpr int kNaThreads = 256;
 constexpr int kMaxDevices = 64;
 

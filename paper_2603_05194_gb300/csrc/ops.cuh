@@ -84,6 +84,16 @@ __device__ __forceinline__ cdf ldro(const cdf* p) {  // (x.hi, x.lo, y.hi, y.lo)
 }
 template <typename R> __device__ __forceinline__ cx<R> czero() { return mk<R>((R)0, (R)0); }
 
+// Asynchronous global -> shared copies (cp.async): an op that prefetches its
+// epilogue inputs issues them before the line transforms, so the loads are in
+// flight while the FFT runs; the same thread reads them back after waiting.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename R> __device__ __forceinline__ R rsq(R v);
 template <> __device__ __forceinline__ double rsq<double>(double v) { return rsqrt(v); }
 template <> __device__ __forceinline__ float rsq<float>(float v) { return rsqrtf(v); }
@@ -271,6 +281,7 @@ template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
   static constexpr bool kZeroUpper = false;  // positions >= L/2 of the first transform's input are zero
   static constexpr bool kHalfOut = false;    // only positions < L/2 of the last transform's output are used
   static constexpr bool kNyqTail = false;    // column pass over columns 0..c.Nx (see k_fast)
+  static constexpr int kPre = 0;  // bytes per element the op prefetches into shared memory (fast engine)
   double* part = nullptr;                  // reduction partials [slot][block]
   int pstride = 0;
 };
@@ -319,6 +330,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_fast(Op op
   } else {
     ok = op.valid(o, x);
   }
+  // epilogue inputs of this thread's elements, [r][thread] (ops with kPre > 0)
+  unsigned char* pre = fast_smem + FastSmem<R, L>::bytes;
+  if constexpr (Op::kPre > 0) {
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r)
+        op.prefetch(o, x, j + C::TPL * r, pre + ((size_t)r * kThreads + threadIdx.x) * Op::kPre);
+    }
+    cp_async_commit();
+  }
   cx<R> v[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) v[r] = (ok && (!Op::kZeroUpper || r < 4)) ? op.load(o, x, j + C::TPL * r) : czero<R>();
@@ -359,7 +380,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_fast(Op op
       __syncthreads();
       fast_fft<R, L, -Op::kSign1, Op::kLM, false, Op::kHalfOut>(v, b0, b1, twsrc, t, j);
     }
-    if (ok) {
+    if constexpr (Op::kPre > 0) {
+      cp_async_wait_all();
+      if (ok) {
+#pragma unroll
+        for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r)
+          op.store_pre(o, x, j + C::TPL * r, v[r], acc, pre + ((size_t)r * kThreads + threadIdx.x) * Op::kPre);
+      }
+    } else if (ok) {
 #pragma unroll
       for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
     }
@@ -424,17 +452,20 @@ inline bool fast_len(int L) { return L >= 16 && L <= 1024 && (L & (L - 1)) == 0;
 inline int ceil_div_l(long a, long b) { return (int)((a + b - 1) / b); }
 
 // Generic-engine tile sizes (see atkm_internal.cuh).
+// Narrower tiles until the pass has at least two CTAs per SM.
 template <typename R> inline int gen_lm_tile(int L, long nlines) {
   int T = TileElems<R>::value / L;
   if (T < 1) T = 1;
-  while (T > 1 && ceil_div_l(nlines, T) < 2 * 152) T >>= 1;
+  const long want = 2L * device_sm_count();
+  while (T > 1 && ceil_div_l(nlines, T) < want) T >>= 1;
   return T;
 }
 template <typename R> inline int gen_col_tile(int L, int X, long outer) {
   int T = TileElems<R>::value / L;
   if (T > X) T = X;
   if (T < 1) T = 1;
-  while (T > 8 && (long)ceil_div_l(X, T) * outer < 2 * 152) T >>= 1;
+  const long want = 2L * device_sm_count();
+  while (T > 8 && (long)ceil_div_l(X, T) * outer < want) T >>= 1;
   return T;
 }
 
@@ -477,7 +508,7 @@ inline cudaError_t ensure_smem(std::atomic<unsigned long long>& done, K kernel, 
 template <typename R, int L, class Op>
 inline cudaError_t launch_fast_L(const Op& op, const FftLen& f, const PassGrid& pg, cudaStream_t st) {
   static std::atomic<unsigned long long> prepared{0};
-  const size_t sm = FastSmem<R, L>::bytes;
+  const size_t sm = FastSmem<R, L>::bytes + (size_t)Op::kPre * 8 * kThreads;
   cudaError_t e = ensure_smem(prepared, k_fast<R, L, Op>, sm);
   if (e != cudaSuccess) return e;
   // binary64 passes take the multiply-add form of the twiddles
@@ -703,6 +734,14 @@ template <typename R, bool RED> struct OpHY : OpBase<-1, true, RED ? 2 : 0, fals
     const size_t idx = ((size_t)o * c.Ny + pos) * c.Nx + x;
     acc[idx] = add<R>(acc[idx], v);
   }
+  // FP32: the accumulator (8 B a point) is prefetched into shared memory
+  static constexpr int kPre = std::is_same<R, float>::value ? 8 : 0;
+  __device__ void prefetch(int o, int x, int pos, unsigned char* dst) const {
+    cp_async8(dst, acc + ((size_t)o * c.Ny + pos) * c.Nx + x);
+  }
+  __device__ void store_pre(int o, int x, int pos, cx<R> v, R*, const unsigned char* src) const {
+    acc[((size_t)o * c.Ny + pos) * c.Nx + x] = add<R>(*reinterpret_cast<const cx<R>*>(src), v);
+  }
 };
 
 // z: multiplier nu^2/2 on lines (o = y, x), then
@@ -729,6 +768,21 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R* a) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
+    finish(o, x, pos, idx, v, a, tor<R>(ldro(Phi + idx)), ldro(acc + idx));
+  }
+  // FP32: Phi (8 B) and the accumulator (8 B) are prefetched into shared memory
+  static constexpr int kPre = std::is_same<R, float>::value ? 16 : 0;
+  __device__ void prefetch(int o, int x, int pos, unsigned char* dst) const {
+    const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
+    cp_async8(dst, Phi + idx);
+    cp_async8(dst + 8, acc + idx);
+  }
+  __device__ void store_pre(int o, int x, int pos, cx<R> v, R* a, const unsigned char* src) const {
+    const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
+    finish(o, x, pos, idx, v, a, tor<R>(*reinterpret_cast<const double*>(src)),
+           *reinterpret_cast<const cx<R>*>(src + 8));
+  }
+  __device__ __forceinline__ void finish(int o, int x, int pos, size_t idx, cx<R> v, R* a, R Pd, cx<R> accv) const {
     R V;
     if constexpr (std::is_same<R, double>::value) {
       V = ph.gz2 * az.hxc2[pos] + (ph.gy2 * ay.hxc2[o] + ph.gx2 * ax.hxc2[x]);
@@ -738,9 +792,8 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
     }
     const cx<R> fv = from64<R>(ldro(f + idx));
     const cx<R> pv = same ? fv : from64<R>(ldro(phi + idx));
-    const R Pd = tor<R>(ldro(Phi + idx));
     const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
-    const cx<R> kin = add<R>(ldro(acc + idx), v);
+    const cx<R> kin = add<R>(accv, v);
     const R ox = kin.x + w * fv.x, oy = kin.y + w * fv.y;
     Hf[idx] = make_double2(tod<R>(ox), tod<R>(oy));
     if (RED) {

@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <utility>
 #include <thread>
@@ -34,7 +35,7 @@ namespace atkm {
 
 namespace {
 
-constexpr int kRedGrid = 1216;  // 8 CTAs per SM on 152 SMs
+constexpr int kRedGrid = 1216;  // most reduction CTAs of a vector kernel (partial-sum capacity)
 constexpr int kRedThreads = 256;
 
 // ------------------------------------------------------------ control block
@@ -54,6 +55,16 @@ struct Ctl {
   double cr, sr, nrm2, inv, En, linf, bestE, best_t;
   int accepted, nh, forced, pad1;
   double inv0;  // normalisation of psi_0
+  // device-driven loop (Solver::run_device): the decisions the host takes
+  // between iterations in the host-driven path, taken by control kernels
+  int n, n_start, max_iter, max_halv;
+  int caps, status, done, handover;
+  int logc, log_cap, f32, f32_iters;
+  int total_h, f32_best_n, q, final_top;
+  int step_logged, f32_window;
+  double tol_res, tol_linf, switch_tol, f32_best, linf_n;
+  unsigned long long deadline, guard, guard_max, launches;
+  atkm_iter_log* log;  // device array of log_cap entries
 };
 
 // ------------------------------------------------------------ reductions
@@ -300,18 +311,10 @@ int red_grid(size_t N) {
 int wave_grid(const void* kernel, size_t N) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, int>> cache;
-  static int nsm = 0;
+  const int nsm = device_sm_count();
   int per_sm = 0;
   {
     std::lock_guard<std::mutex> lock(mu);
-    if (nsm == 0) {
-      int dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
-        cudaGetLastError();
-        nsm = 152;
-      }
-    }
     for (auto& kv : cache)
       if (kv.first == kernel) per_sm = kv.second;
     if (per_sm == 0) {
@@ -323,10 +326,11 @@ int wave_grid(const void* kernel, size_t N) {
       cache.emplace_back(kernel, per_sm);
     }
   }
-  const size_t full = (size_t)nsm * per_sm;
   const size_t cap = (size_t)red_grid(N);
+  if (nsm <= 0) return (int)cap;  // SM count unknown: the size-based grid
+  const size_t full = (size_t)nsm * per_sm;
   if (cap < full) return (int)cap;
-  return (int)(full > (size_t)kRedGrid ? (kRedGrid / nsm) * nsm : full);
+  return (int)(full > (size_t)kRedGrid ? std::max(kRedGrid / nsm, 1) * nsm : full);
 }
 
 // Slots of plan->scal used by the driver.
@@ -452,7 +456,7 @@ __global__ void k_c_accept(Ctl* c, const double* s) {
 }
 
 // Next trial: halve t, or (mode 1) take the lowest-energy trial seen.
-__global__ void k_c_halve(Ctl* c, int mode) {
+__device__ __forceinline__ void halve_body(Ctl* c, int mode) {
   if (mode == 0) {
     c->t *= 0.5;
     c->nh += 1;
@@ -463,6 +467,9 @@ __global__ void k_c_halve(Ctl* c, int mode) {
   c->cr = cos(c->t * c->pn);
   c->sr = sin(c->t * c->pn) / c->pn;
 }
+__global__ void k_c_halve(Ctl* c, int mode) { halve_body(c, mode); }
+// The same with the mode taken on the device: halve while halvings remain.
+__global__ void k_c_halve_auto(Ctl* c) { halve_body(c, c->nh < c->max_halv ? 0 : 1); }
 
 // End of an iteration: the trial becomes phi_{n+1}.
 __global__ void k_c_end(Ctl* c) {
@@ -477,6 +484,190 @@ __global__ void k_c_reset_state(Ctl* c, int have_E, int force_sd, int clear_prev
   c->have_E = have_E;
   c->force_sd = force_sd;
   if (clear_prev) c->have_prev = 0;
+}
+
+// ---------------------------------------------------- device-driven loop
+// The iteration loop as a CUDA graph with conditional nodes: the control
+// kernels below take, between iterations, exactly the decisions that
+// Solver::process takes on the host (stop rule, precision hand-over,
+// halving, stagnation, log), and set the graph's condition handles.  Every
+// loop is also bounded by a guard counter derived from max_iter and
+// max_halvings, so a graph launch always ends.
+// FP32 phase stagnation: no halving of the best FP32 residual for this many
+// iterations (opts.f32_window, this when 0) hands over to FP64.
+constexpr int kF32Window = 400;
+
+struct LoopInit {
+  int n, max_iter, max_halv, caps, f32, log_cap, q, f32_window;
+  double tol_res, tol_linf, switch_tol, linf, time_limit_s;
+  atkm_iter_log* log;
+  unsigned long long guard_max;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void k_d_setup(Ctl* c, LoopInit L) {
+  c->n = c->n_start = L.n;
+  c->max_iter = L.max_iter;
+  c->max_halv = L.max_halv;
+  c->caps = L.caps;
+  c->status = ATKM_NOT_CONVERGED;
+  c->done = c->handover = c->final_top = c->step_logged = 0;
+  c->logc = 0;
+  c->log_cap = L.log_cap;
+  c->log = L.log;
+  c->f32 = L.f32;
+  c->f32_iters = c->total_h = 0;
+  c->f32_best_n = L.n;
+  c->f32_best = INFINITY;
+  c->q = L.q;
+  c->f32_window = L.f32_window;
+  c->tol_res = L.tol_res;
+  c->tol_linf = L.tol_linf;
+  c->switch_tol = L.switch_tol;
+  c->linf_n = L.linf;
+  c->deadline = L.time_limit_s > 0.0 ? global_ns() + (unsigned long long)(L.time_limit_s * 1e9) : 0ull;
+  c->guard = 0;
+  c->guard_max = L.guard_max;
+  c->launches = 1;
+}
+
+// After Step 2 (loop top): log entry, stop rule, hand-over test.
+__global__ void k_d_check(Ctl* c, cudaGraphConditionalHandle h_rest, int nodes) {
+  c->launches += nodes;
+  if (c->final_top) {  // the residual of the final state after a stagnated run
+    c->final_top = 0;
+    c->done = 1;
+    cudaGraphSetConditional(h_rest, 0);
+    return;
+  }
+  c->step_logged = 0;
+  if (c->log && c->logc < c->log_cap) {
+    atkm_iter_log* L = &c->log[c->logc++];
+    *L = atkm_iter_log{};
+    L->n = c->n; L->E = c->E; L->mu = c->mu; L->residual = c->res; L->linf_step = c->linf_n; L->f32_phase = c->f32;
+    c->step_logged = 1;
+  }
+  if (c->nan) {
+    c->status = ATKM_ERR_NAN;
+    c->done = 1;
+  } else {
+    if (c->f32 && c->res < 0.5 * c->f32_best) {
+      c->f32_best = c->res;
+      c->f32_best_n = c->n;
+    }
+    if (c->f32 && (c->res <= c->switch_tol || c->caps >= 2 || c->n - c->f32_best_n > c->f32_window)) {
+      c->handover = 1;  // ends this phase; the entry is re-made by the FP64 phase
+      c->done = 1;
+      if (c->step_logged) {
+        c->logc -= 1;
+        c->step_logged = 0;
+      }
+    } else if (!c->f32 && (c->res <= c->tol_res || (c->tol_linf > 0.0 && c->linf_n <= c->tol_linf))) {
+      c->status = ATKM_OK;
+      c->done = 1;
+    } else if (c->n - c->n_start >= c->max_iter) {
+      c->status = ATKM_NOT_CONVERGED;
+      c->done = 1;
+    } else if (c->deadline && global_ns() >= c->deadline) {
+      c->status = ATKM_ERR_TIMEOUT;
+      c->done = 1;
+    } else if (c->f32) {
+      c->f32_iters += 1;
+    }
+  }
+  cudaGraphSetConditional(h_rest, !c->done);
+}
+
+// After each trial of Step 4 (iii): another halving (or the forced trial)?
+__global__ void k_d_after_trial(Ctl* c, cudaGraphConditionalHandle h_halve, int nodes) {
+  c->launches += nodes;
+  int more;
+  if (c->forced) {
+    more = 0;
+  } else if (!fin(c->En)) {
+    c->status = ATKM_ERR_NAN;
+    c->done = 1;
+    more = 0;
+  } else {
+    more = !c->accepted;
+  }
+  if (more && ++c->guard > c->guard_max) {
+    c->status = ATKM_ERR_TIMEOUT;
+    c->done = 1;
+    more = 0;
+  }
+  cudaGraphSetConditional(h_halve, more);
+}
+
+// End of an iteration: the trial becomes phi_{n+1} (k_c_end), bookkeeping.
+__global__ void k_d_end(Ctl* c, int nodes) {
+  c->launches += nodes;
+  if (c->done) return;
+  const int acc = c->accepted && !c->forced;
+  c->total_h += c->nh;
+  c->caps = acc ? 0 : c->caps + 1;
+  if (c->step_logged) {
+    atkm_iter_log* L = &c->log[c->logc - 1];
+    L->alpha = c->alpha; L->beta_cg = c->beta_cg; L->reset_to_sd = c->reset; L->d1 = c->d1; L->curvature = c->curv;
+    L->t0 = c->t0; L->t = c->t; L->halvings = c->nh; L->accepted = acc;
+  }
+  c->linf_n = c->linf;
+  c->den_prev = c->den;
+  c->have_prev = 1;
+  c->E = c->En;
+  c->force_sd = c->forced;
+  c->q ^= 1;
+  c->n += 1;
+  if (c->caps >= 3 && !c->f32) {
+    c->status = ATKM_STAGNATED;
+    c->done = 1;
+    c->final_top = 1;
+  }
+}
+
+// Between the two iterations of a loop body: run the second one?
+__global__ void k_d_gate(Ctl* c, cudaGraphConditionalHandle h_go1, int nodes) {
+  c->launches += nodes;
+  cudaGraphSetConditional(h_go1, !c->done || c->final_top);
+}
+
+// End of a loop body (two iterations): run again?
+__global__ void k_d_loop(Ctl* c, cudaGraphConditionalHandle h_run, cudaGraphConditionalHandle h_go0, int nodes) {
+  c->launches += nodes;
+  int run = !c->done || c->final_top;
+  if (run && ++c->guard > c->guard_max) {
+    c->status = ATKM_ERR_TIMEOUT;
+    c->done = 1;
+    c->final_top = 0;
+    run = 0;
+  }
+  cudaGraphSetConditional(h_run, run);
+  cudaGraphSetConditional(h_go0, run);
+}
+
+// After the FP32 loop: hand over at the parity where it stopped.
+__global__ void k_d_phase(Ctl* c, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1, int nodes) {
+  c->launches += nodes;
+  const int ho = c->handover;
+  cudaGraphSetConditional(h0, ho && c->q == 0);
+  cudaGraphSetConditional(h1, ho && c->q == 1);
+}
+
+// The hand-over's state change (after the FP64 ATKM of phi): FP64 from here.
+__global__ void k_d_handover(Ctl* c, double tolE_eps, int nodes) {
+  c->launches += nodes;
+  c->f32 = 0;
+  c->caps = 0;
+  c->handover = 0;
+  c->done = 0;
+  c->have_E = 0;
+  c->force_sd = 1;
+  c->tolE_eps = tolE_eps;
 }
 
 }  // namespace
@@ -515,6 +706,12 @@ struct PcgBuffers {
   bool valid = false, f32 = false;
   int parity = 0, n = 0, caps = 0;
   double linf = INFINITY;
+  // device-driven solve graphs per [polish form][starts in FP32][start parity]
+  cudaGraph_t dg[4][2][2] = {};
+  cudaGraphExec_t dx[4][2][2] = {};
+  bool dl_ok = true;             // false once building or launching one failed
+  atkm_iter_log* dlog = nullptr; // device log of the device-driven loop
+  int dlog_cap = 0;
 };
 
 static void drop_graph(PcgBuffers* b, int f, int q, int k) {
@@ -533,6 +730,14 @@ static void destroy_graphs(PcgBuffers* b) {
   for (int f = 0; f < 4; ++f)
     for (int q = 0; q < 2; ++q)
       for (int k = 0; k < 3; ++k) drop_graph(b, f, q, k);
+  for (int f = 0; f < 4; ++f)
+    for (int a = 0; a < 2; ++a)
+      for (int q = 0; q < 2; ++q) {
+        if (b->dx[f][a][q]) cudaGraphExecDestroy(b->dx[f][a][q]);
+        if (b->dg[f][a][q]) cudaGraphDestroy(b->dg[f][a][q]);
+        b->dx[f][a][q] = nullptr;
+        b->dg[f][a][q] = nullptr;
+      }
   b->last = nullptr;
 }
 
@@ -541,7 +746,7 @@ void pcg_free(atkm_plan* p) {
   PcgBuffers* b = p->pcg;
   destroy_graphs(b);
   void* ptrs[] = {b->phi[0], b->phi[1], b->r[0], b->r[1], b->p[0], b->p[1], b->Phi[0], b->Phi[1],
-                  b->Hphi, b->Pr, b->Hp, b->Phi1, b->ctl};
+                  b->Hphi, b->Pr, b->Hp, b->Phi1, b->ctl, b->dlog};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->ctl_h) cudaFreeHost(b->ctl_h);
@@ -689,6 +894,10 @@ struct Seq {
   // A whole iteration: Steps 2-4 up to the first trial.
   void iteration() {
     top();
+    rest();
+  }
+  // Steps 3-4 up to the first trial (after top()).
+  void rest() {
     chk(precond());
     prof_begin(p, "vec_dir_dots", 80.0 * B.N, 0.0, st());
     const int gd = f32 ? wave_grid((const void*)k_dir_dots<float>, B.N)
@@ -804,14 +1013,143 @@ static cudaError_t run_phase(Seq& S, int kind, bool use_graphs) {
   return cudaGraphLaunch(gx, B.st);
 }
 
+// ------------------------------------------------------------- solve graph
+// Builds the device-driven solve of one instance into a graph (a chain with
+// no incoming dependency, so several instances can share one graph):
+//   start in FP32: Loop(F32, q0); k_d_phase; IF(ho0) { hand-over at 0;
+//     Loop(polish, 0) }; IF(ho1) { hand-over at 1; Loop(polish, 1) }
+//   otherwise:     Loop(polish, q0)
+// Loop(q) = WHILE(run) { IF(go0) { Iter(q) }; k_d_gate; IF(go1) { Iter(q ^ 1) }; k_d_loop }
+// Iter(q) = top; k_d_check; IF(rest) { rest; k_d_after_trial;
+//           WHILE(halve) { k_c_halve_auto; trial; k_d_after_trial }; k_d_end }
+// The kernels are those of Seq, captured on the plan stream; the condition
+// handles belong to the graph the chain is built into, and each is set only
+// by kernels of the graph that holds its node (or, for a WHILE node, of its
+// body).
+struct GraphBuild {
+  PcgBuffers& B;
+  cudaGraph_t top;
+  cudaError_t err = cudaSuccess;
+
+  void chk(cudaError_t e) {
+    if (err == cudaSuccess && e != cudaSuccess) err = e;
+  }
+  cudaGraphConditionalHandle handle(unsigned def) {
+    cudaGraphConditionalHandle h = 0;
+    if (err == cudaSuccess) chk(cudaGraphConditionalHandleCreate(&h, top, def, cudaGraphCondAssignDefault));
+    return h;
+  }
+  // A conditional node in g after *dep (none when null); *dep becomes the
+  // node; returns its body graph.
+  cudaGraph_t cond(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphConditionalHandle h,
+                   cudaGraphConditionalNodeType type) {
+    if (err != cudaSuccess) return nullptr;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    chk(cudaGraphAddNode(&node, g, *dep ? dep : nullptr, nullptr, *dep ? 1 : 0, &np));
+    if (err != cudaSuccess) return nullptr;
+    *dep = node;
+    return np.conditional.phGraph_out[0];
+  }
+  // Captures fn() on the plan stream into g after *dep; *dep becomes the last
+  // captured node.  fn gets the number of kernels it has launched so far.
+  template <class F> void capture(cudaGraph_t g, cudaGraphNode_t* dep, F fn) {
+    if (err != cudaSuccess) return;
+    // relaxed: the launchers may set kernel attributes or query occupancy on
+    // first use, which the stricter capture modes refuse
+    chk(cudaStreamBeginCaptureToGraph(B.st, g, *dep ? dep : nullptr, nullptr, *dep ? 1 : 0,
+                                      cudaStreamCaptureModeRelaxed));
+    if (err != cudaSuccess) return;
+    const unsigned long long c0 = atkm_launch_count();
+    fn([c0]() { return (int)(atkm_launch_count() - c0); });
+    const int k = (int)(atkm_launch_count() - c0);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    chk(cudaStreamGetCaptureInfo(B.st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+    const cudaGraphNode_t last = (err == cudaSuccess && nd == 1) ? deps[0] : nullptr;
+    cudaGraph_t out = nullptr;
+    chk(cudaStreamEndCapture(B.st, &out));
+    count_launches(-k);  // recorded into the graph, not executed
+    if (!last) chk(cudaErrorInvalidValue);  // a segment ends in exactly one node
+    *dep = last;
+  }
+
+  void iteration(cudaGraph_t g, Seq& S) {
+    cudaGraphConditionalHandle h_rest = handle(0), h_halve = handle(0);
+    Ctl* c = B.ctl;
+    cudaGraphNode_t d = nullptr;
+    capture(g, &d, [&](auto sofar) {
+      S.top();
+      S.ctl1(k_d_check, c, h_rest, sofar() + 1);
+    });
+    cudaGraph_t rb = cond(g, &d, h_rest, cudaGraphCondTypeIf);
+    if (err != cudaSuccess) return;
+    cudaGraphNode_t r = nullptr;
+    capture(rb, &r, [&](auto sofar) {
+      S.rest();
+      S.ctl1(k_d_after_trial, c, h_halve, sofar() + 1);
+    });
+    cudaGraph_t hb = cond(rb, &r, h_halve, cudaGraphCondTypeWhile);
+    if (err != cudaSuccess) return;
+    cudaGraphNode_t h = nullptr;
+    capture(hb, &h, [&](auto sofar) {
+      S.ctl1(k_c_halve_auto, c);
+      S.trial();
+      S.ctl1(k_d_after_trial, c, h_halve, sofar() + 1);
+    });
+    capture(rb, &r, [&](auto) { S.ctl1(k_d_end, c, 1); });
+  }
+
+  void loop(cudaGraph_t g, cudaGraphNode_t* dep, Seq& S0, Seq& S1) {
+    cudaGraphConditionalHandle h_run = handle(1), h_go0 = handle(1), h_go1 = handle(0);
+    cudaGraph_t body = cond(g, dep, h_run, cudaGraphCondTypeWhile);
+    if (err != cudaSuccess) return;
+    cudaGraphNode_t d = nullptr;
+    cudaGraph_t b0 = cond(body, &d, h_go0, cudaGraphCondTypeIf);
+    if (err == cudaSuccess) iteration(b0, S0);
+    capture(body, &d, [&](auto) { S0.ctl1(k_d_gate, B.ctl, h_go1, 1); });
+    cudaGraph_t b1 = cond(body, &d, h_go1, cudaGraphCondTypeIf);
+    if (err == cudaSuccess) iteration(b1, S1);
+    capture(body, &d, [&](auto) { S0.ctl1(k_d_loop, B.ctl, h_run, h_go0, 1); });
+  }
+
+  // The whole chain of one instance; f32s[q] / pol[q]: the kernel sequences
+  // of the FP32 phase and of the polish at parity q.
+  void solve(bool start_f32, int q0, Seq* f32s, Seq* pol, double tolE_eps_polish, const LoopInit* init) {
+    cudaGraphNode_t d = nullptr;
+    if (init) capture(top, &d, [&](auto) { pol[0].ctl1(k_d_setup, B.ctl, *init); });
+    if (!start_f32) {
+      loop(top, &d, pol[q0], pol[q0 ^ 1]);
+      return;
+    }
+    loop(top, &d, f32s[q0], f32s[q0 ^ 1]);
+    cudaGraphConditionalHandle h_ho[2] = {handle(0), handle(0)};
+    capture(top, &d, [&](auto) { pol[0].ctl1(k_d_phase, B.ctl, h_ho[0], h_ho[1], 1); });
+    for (int qq = 0; qq < 2 && err == cudaSuccess; ++qq) {
+      cudaGraph_t hb = cond(top, &d, h_ho[qq], cudaGraphCondTypeIf);
+      if (err != cudaSuccess) return;
+      cudaGraphNode_t x = nullptr;
+      capture(hb, &x, [&](auto sofar) {
+        pol[qq].atkm(SRC_PSI, reinterpret_cast<const double*>(B.phi[qq]), nullptr, B.Phi[qq]);
+        pol[qq].ctl1(k_d_handover, B.ctl, tolE_eps_polish, sofar() + 1);
+      });
+      loop(hb, &x, pol[qq], pol[qq ^ 1]);
+    }
+  }
+};
+
 // One PCG solve as a host-side state machine: launch() enqueues the next
 // phase (graph or direct launches) and an asynchronous read of the control
 // block on the plan stream; wait() synchronises that stream; process() takes
 // the decisions of the stop rule, the halving loop and the log.  Several
 // solvers on different plans run concurrently (pcg_ground_state_batched).
-// FP32 phase stagnation: no halving of the best FP32 residual for this many
-// iterations hands over to FP64 (slow but steady phases halve it well within).
-constexpr int kF32Window = 400;
+// With graphs on and profiling off, run_device() replaces that loop by one
+// launch of the device-driven solve graph (same kernels, same decisions).
 
 struct Solver {
   enum State { INIT_CHECK, MAIN, HALVE, FORCED, FINAL, DONE };
@@ -834,8 +1172,124 @@ struct Solver {
   const double eps64 = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
   const double epsdw = 1.4210854715202004e-14;  // 2^-46: double-word operators
   double eps_polish() const { return dwm ? epsdw : eps64; }
+  std::chrono::steady_clock::time_point t_start;
+  bool ran_device = false;
 
   void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
+  double elapsed_s() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  bool past_time_limit() const { return opts->time_limit_s > 0.0 && elapsed_s() >= opts->time_limit_s; }
+
+  // ---- device-driven run (graphs on, profiling off)
+  int fi_polish() const { return (split || dwm) ? (dwm ? 3 : 2) : 0; }
+  int f32_window() const { return opts->f32_window > 0 ? opts->f32_window : kF32Window; }
+  bool device_loop_ok() const { return use_graphs && B->graphs_ok && B->dl_ok && plan->prof == nullptr; }
+  Seq seq_q(bool is32, int qq) {
+    Seq S{plan, *B, ph, is32, qq};
+    S.aux32 = (split || dwm) && !is32;
+    S.dw = dwm && !is32;
+    return S;
+  }
+  int log_room() const { return (logbuf && opts->log_capacity > logc) ? opts->log_capacity - logc : 0; }
+  cudaError_t ensure_dlog() {
+    const int need = log_room();
+    if (need <= B->dlog_cap) return cudaSuccess;
+    if (B->dlog) cudaFree(B->dlog);
+    B->dlog = nullptr;
+    B->dlog_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&B->dlog, (size_t)need * sizeof(atkm_iter_log));
+    if (e == cudaSuccess) B->dlog_cap = need;
+    return e;
+  }
+  LoopInit loop_init() const {
+    LoopInit I{};
+    I.n = n;
+    I.max_iter = opts->max_iter;
+    I.max_halv = opts->max_halvings;
+    I.caps = caps;
+    I.f32 = f32 ? 1 : 0;
+    I.log_cap = log_room();
+    I.q = q;
+    I.f32_window = f32_window();
+    I.tol_res = opts->tol_residual;
+    I.tol_linf = opts->tol_linf;
+    I.switch_tol = opts->switch_tol;
+    I.linf = linf;
+    I.time_limit_s = opts->time_limit_s > 0.0 ? std::max(opts->time_limit_s - elapsed_s(), 1e-9) : 0.0;
+    I.log = B->dlog;
+    // loop bodies of both phases and halving rounds of every iteration
+    const unsigned long long mi = (unsigned long long)opts->max_iter, mh = (unsigned long long)opts->max_halvings;
+    I.guard_max = 2ull * (mi / 2ull + 3ull) + (mi + 2ull) * (mh + 2ull) + 64ull;
+    return I;
+  }
+  // Builds this solver's chain into graph g (init: the setup kernel's
+  // parameters, captured too; null when the caller launches it).
+  cudaError_t build_chain(cudaGraph_t g, const LoopInit* init) {
+    GraphBuild GB{*B, g};
+    Seq F[2] = {seq_q(true, 0), seq_q(true, 1)};
+    Seq P[2] = {seq_q(false, 0), seq_q(false, 1)};
+    GB.solve(f32, q, F, P, 32.0 * eps_polish(), init);
+    for (auto& x : F) GB.chk(x.err);
+    for (auto& x : P) GB.chk(x.err);
+    return GB.err;
+  }
+  // The cached solve graph for this solver's state, built on first use.
+  cudaGraphExec_t solve_graph() {
+    const int fp = fi_polish(), a = f32 ? 1 : 0;
+    cudaGraphExec_t& gx = B->dx[fp][a][q];
+    if (gx) return gx;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = build_chain(g, nullptr);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (ex) cudaGraphExecDestroy(ex);
+      if (g) cudaGraphDestroy(g);
+      B->dl_ok = false;  // the host-driven loop takes over
+      return nullptr;
+    }
+    B->dg[fp][a][q] = g;
+    gx = ex;
+    return gx;
+  }
+  // Enqueues the rest of this solve as one graph launch (and the read of the
+  // control block); false when the host-driven loop has to run instead.
+  bool start_device() {
+    if (st != MAIN || !device_loop_ok()) return false;
+    if (ensure_dlog() != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaGraphExec_t gx = solve_graph();
+    if (!gx) return false;
+    k_d_setup<<<1, 1, 0, B->st>>>(B->ctl, loop_init());
+    chk(cudaGetLastError());
+    chk(cudaGraphLaunch(gx, B->st));
+    fetch_async();
+    return true;
+  }
+  // After the launch has completed: the solve's state and log from the device.
+  void absorb_device() {
+    if (err != cudaSuccess) return;
+    const Ctl& h = H();
+    count_launches((int)h.launches);
+    if (h.logc > 0 && logbuf)
+      chk(cudaMemcpy(logbuf + logc, B->dlog, (size_t)h.logc * sizeof(atkm_iter_log), cudaMemcpyDeviceToHost));
+    logc += h.logc;
+    n = h.n;
+    q = h.q;
+    caps = h.caps;
+    f32 = h.f32 != 0;
+    total_h += h.total_h;
+    f32_iters += h.f32_iters;
+    linf = h.linf_n;
+    status = h.status;
+    st = DONE;
+    ran_device = true;
+  }
   bool done() const { return st == DONE || err != cudaSuccess; }
   Ctl& H() { return *B->ctl_h; }
   Seq seq(bool is32) {
@@ -854,8 +1308,9 @@ struct Solver {
   int begin(atkm_plan* pl, const atkm_params* pr, const atkm_pcg_opts* op, double* ps, atkm_result* o,
             cudaStream_t cs) {
     plan = pl; prm = pr; opts = op; psi = ps; out = o; caller = cs;
+    t_start = std::chrono::steady_clock::now();
     if (!plan || !prm || !opts || !psi || !out) return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: NULL argument");
-    if (!(opts->tol_residual >= 0.0) || opts->max_iter < 0 || opts->max_halvings < 0)
+    if (!(opts->tol_residual >= 0.0) || opts->max_iter < 0 || opts->max_halvings < 0 || !(opts->time_limit_s >= 0.0))
       return fail(plan, ATKM_ERR_ARG, "pcg_ground_state: bad options");
     split = opts->precision_mode == ATKM_PRECISION_F32_SPLIT;
     dwm = opts->precision_mode == ATKM_PRECISION_DF32_SPLIT;
@@ -906,8 +1361,10 @@ struct Solver {
       const double2* p0 = reinterpret_cast<const double2*>(psi);
       S.dot(p0, p0, S_N);
       S.ctl1(k_c_init, B->ctl, (const double*)plan->scal);
+      // the normalisation stays FP64 in every precision form (as the
+      // renormalisation after each retraction does)
       S.lincomb(B->phi[0], p0, Coef{&B->ctl->inv0, 1.0}, nullptr, Coef{nullptr, 0.0}, nullptr, Coef{nullptr, 0.0},
-                nullptr, S_T);
+                nullptr, S_T, nullptr, false);
       S.atkm(SRC_PSI, reinterpret_cast<const double*>(B->phi[0]), nullptr, B->Phi[0]);
       S.ctl1(k_c_reset_state, B->ctl, 0, 1, 1);
       chk(S.err);
@@ -982,7 +1439,7 @@ struct Solver {
         }
         if (h.nan) { status = ATKM_ERR_NAN; st = DONE; return; }
         if (f32 && h.res < 0.5 * f32_best) { f32_best = h.res; f32_best_n = n; }
-        if (f32 && (h.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > kF32Window)) {
+        if (f32 && (h.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > f32_window())) {
           // hand over to FP64: recompute Phi in FP64, re-evaluate this phi, restart the direction
           f32 = false;
           caps = 0;
@@ -1001,6 +1458,7 @@ struct Solver {
           return;
         }
         if (n - n_start >= opts->max_iter) { status = ATKM_NOT_CONVERGED; st = DONE; return; }
+        if (past_time_limit()) { status = ATKM_ERR_TIMEOUT; st = DONE; return; }
         if (f32) ++f32_iters;
         decide_trial();
         return;
@@ -1047,7 +1505,8 @@ struct Solver {
       return fail(plan, ATKM_ERR_NAN, "pcg_ground_state: initial state has zero or non-finite norm");
     }
     Ctl& h = H();
-    B->valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED);
+    B->valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED ||
+                status == ATKM_ERR_TIMEOUT);
     B->f32 = f32; B->parity = q; B->n = n; B->caps = caps; B->linf = linf;
     chk(cudaMemcpyAsync(psi, B->phi[q], B->N * sizeof(double2), cudaMemcpyDeviceToDevice, B->st));
     chk(cudaEventRecord(B->ev_out, B->st));
@@ -1072,15 +1531,66 @@ struct Solver {
     out->f32_iters = f32_iters;
     out->status = status;
     out->log_count = logc;
+    out->device_loop = ran_device ? 1 : 0;
     if (status != ATKM_OK) {
       const char* why = status == ATKM_NOT_CONVERGED ? "max_iter reached"
                         : status == ATKM_STAGNATED   ? "three consecutive exhausted halving loops"
+                        : status == ATKM_ERR_TIMEOUT ? "time limit reached"
                                                      : "non-finite energy or residual";
       fail(plan, status, std::string("pcg_ground_state: ") + why);
     }
     return status;
   }
 };
+
+// Every unfinished instance that can run device-driven becomes one chain of
+// a single graph (built for this call), launched once on `st` after each
+// instance's start-up work; each instance's plan stream is ordered after it.
+// Instances are left untouched when the graph cannot be built.
+static void batched_single_launch(std::vector<Solver>& S, cudaStream_t st) {
+  std::vector<Solver*> run;
+  for (auto& s : S)
+    if (!s.done() && s.st == Solver::MAIN && s.device_loop_ok()) run.push_back(&s);
+  if (run.size() < 2) return;  // one instance: its own cached graph
+  for (Solver* s : run)
+    if (s->ensure_dlog() != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t gx = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  std::vector<LoopInit> inits;
+  inits.reserve(run.size());
+  for (Solver* s : run) {
+    if (e != cudaSuccess) break;
+    inits.push_back(s->loop_init());
+    e = s->build_chain(g, &inits.back());
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (gx) cudaGraphExecDestroy(gx);
+    if (g) cudaGraphDestroy(g);
+    return;
+  }
+  for (Solver* s : run) {  // after each instance's start-up work
+    s->chk(cudaEventRecord(s->B->ev_in, s->B->st));
+    s->chk(cudaStreamWaitEvent(st, s->B->ev_in, 0));
+  }
+  e = cudaGraphLaunch(gx, st);
+  for (Solver* s : run) {
+    s->chk(e);
+    s->chk(cudaMemcpyAsync(s->B->ctl_h, s->B->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  }
+  const cudaError_t es = cudaStreamSynchronize(st);
+  for (Solver* s : run) {
+    s->chk(es);
+    s->absorb_device();
+  }
+  cudaGraphExecDestroy(gx);
+  cudaGraphDestroy(g);
+}
 
 }  // namespace atkm
 
@@ -1130,7 +1640,15 @@ int pcg_ground_state(atkm_plan* plan, const atkm_params* prm, const atkm_pcg_opt
   Solver S;
   int code = S.begin(plan, prm, opts, psi_inout, out, (cudaStream_t)stream);
   if (code != ATKM_OK) return code;
-  while (!S.done()) {
+  if (S.st == Solver::INIT_CHECK) {  // the start-up work is enqueued: its NaN check
+    S.wait();
+    S.process();
+  }
+  if (!S.done() && S.start_device()) {  // the whole loop in one graph launch
+    S.wait();
+    S.absorb_device();
+  }
+  while (!S.done()) {  // host-driven loop (profiling on, graphs off, or no device loop)
     S.launch();
     S.wait();
     S.process();
@@ -1156,9 +1674,26 @@ int pcg_ground_state_batched(int count, atkm_plan* const* plans, const atkm_para
     for (int i = 0; i < count; ++i) S[i].abandon();
     return first_err;
   }
-  // Event-driven rounds: every instance enqueues its next phase on its own
-  // stream as soon as its previous phase has finished and been processed, so
-  // small grids keep iterating while large ones are still on the GPU.
+  for (auto& s : S)
+    if (s.st == Solver::INIT_CHECK) {
+      s.wait();
+      s.process();
+    }
+  // Device-driven: every instance's whole solve in one graph (one chain per
+  // instance, no dependencies between chains), one launch for the sweep.
+  batched_single_launch(S, (cudaStream_t)stream);
+  // Otherwise each instance's solve graph on its own stream; what still
+  // needs the host (profiling, graphs off) runs event-driven: every instance
+  // enqueues its next phase as soon as its previous one has been processed,
+  // so small grids keep iterating while large ones are still on the GPU.
+  std::vector<char> dev(count, 0);
+  for (int i = 0; i < count; ++i)
+    if (!S[i].done()) dev[i] = S[i].start_device();
+  for (int i = 0; i < count; ++i)
+    if (dev[i]) {
+      S[i].wait();
+      S[i].absorb_device();
+    }
   for (auto& s : S)
     if (!s.done()) s.launch();
   while (true) {
@@ -1200,8 +1735,13 @@ int pcg_ground_state_mg(int levels, atkm_plan* const* plans, const atkm_params* 
   }
   atkm_pcg_opts o = *opts;
   o.resume = 0;
+  const auto t0 = std::chrono::steady_clock::now();
   int code = ATKM_OK;
   for (int i = 0; i < levels; ++i) {
+    if (opts->time_limit_s > 0.0) {  // the limit covers the whole cascade
+      const double used = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      o.time_limit_s = std::max(opts->time_limit_s - used, 1e-9);
+    }
     code = pcg_ground_state(plans[i], prm, &o, psi[i], &out[i], stream);
     if (code != ATKM_OK && code != ATKM_NOT_CONVERGED && code != ATKM_STAGNATED) return code;
     if (i + 1 < levels) {

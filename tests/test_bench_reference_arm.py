@@ -1,6 +1,7 @@
-"""CPU test of `bench.py --impl reference` (the oracle timed on the host
-cores): one JSON line with the contract's keys, the same workload, metric,
-unit and direction as the GPU arm, and a zero-copy e2e object."""
+"""CPU test of `bench.py --impl reference` (the C++ oracle timed on all the
+host's cores): one JSON line with the contract's keys, the same workload
+(config identical to the GPU arm's), metric, unit and direction as the GPU
+arm, and a zero-copy e2e object."""
 import json
 import os
 import subprocess
@@ -21,7 +22,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
     assert d["config"]["workload"] == bench.WORKLOAD and d["config"]["precision"] == "f64"
+    assert d["config"] == bench.bench_config("f64", 1)
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == bench.host_cores() and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -8,12 +8,21 @@ below, so the reference changes nothing at the printed digits).
 
 Observed agreement with the printed E2: 1e-3 - 3e-3 relative at 32^3 and
 1e-5 - 5e-4 at 64^3 and 128^3 (the vortex rows at Omega = 0.8 included); |I| 2.6e-4 - 5.5e-3 (the largest at 128^3
-in Case II, where |I| ~ 4e-6).  Tolerances: E2 2e-3 at 64^3 and 128^3, 1e-2
-at 32^3; |I| 1e-2; on resolved grids (Case I, 128^3 and 256^3) |I| is at round-off
-level in both (paper 1.7e-11 and 1.3e-12), checked as <= 1e-10.  Not checked: the vortex rows at
-32^3 (which under-resolved state the solve lands in depends on the guess;
-the paper's Case I entry there is not the lowest-energy state), and |I| of
-Case II Omega = 0.8 at 128^3 (2.2% apart, not explained).
+in Case II, where |I| ~ 4e-6), and 2.2e-2 for Case II Omega = 0.8 at 128^3.
+|I| = |2 E_kin - 2 E_pot + 3 E_int + 3 E_dip| is a cancellation: where it is
+about 1e-6 of S = 2|E_kin| + 2|E_pot| + 3|E_int| + 3|E_dip|, a relative
+difference d between two evaluations of the energy terms moves it by up to
+d S.  The |I| of that entry does not depend on the stop rule (the same to 7
+digits at residual 1e-8 ... 1e-12); its gap to the printed value, 1.3e-7, is
+3.5e-9 of S, the size of a relative difference of 3e-8 in E_dip alone, and
+the paper does not state the accuracy of its truncated-kernel coefficients
+(ours are within 1e-13 of two independent quadratures).  So |I| is checked to
+max(1e-2 |I_paper|, 1e-8 S).
+Tolerances: E2 2e-3 at 64^3 and 128^3, 1e-2 at 32^3; |I| as above; on
+resolved grids (Case I, 128^3 and 256^3) |I| is at round-off level in both
+(paper 1.7e-11 and 1.3e-12), checked as <= 1e-10.  Not checked: the vortex
+rows at 32^3 (which under-resolved state the solve lands in depends on the
+guess; the paper's Case I entry there is not the lowest-energy state).
 """
 import numpy as np
 import pytest
@@ -62,9 +71,8 @@ def test_table1_errors_and_virial(lib, case, Om):
             tol = 1e-2 if n == 32 else 2e-3
             assert abs(e2 - e2_paper) <= tol * e2_paper, (n, e2, e2_paper)
         vir = abs(r["virial"])
-        if vortex and case == "II" and n == 128:
-            continue  # |I| ~ 5.6e-6 there: 2.2% apart, not explained (E2 agrees to 1e-5)
+        S = 2 * abs(r["E_kin"]) + 2 * abs(r["E_pot"]) + 3 * abs(r["E_int"]) + 3 * abs(r["E_dip"])
         if vir_paper > 1e-9:
-            assert abs(vir - vir_paper) <= 1e-2 * vir_paper, (n, vir, vir_paper)
+            assert abs(vir - vir_paper) <= max(1e-2 * vir_paper, 1e-8 * S), (n, vir, vir_paper, S)
         else:
             assert vir <= 1e-10, (n, vir)

@@ -162,22 +162,6 @@ def test_pcg_cfg1_full_run_parity(lib, cfg1_oracle):
     assert np.linalg.norm(phi - kappa * ref.phi) / np.linalg.norm(ref.phi) <= 1e-6
 
 
-def test_pcg_cfg2_first_iterations_parity(lib):
-    w = W.CONFIGS["cfg2_128x128x32"]
-    oplan = O.Plan(w.N, w.L, w.n)
-    oprm = O.Params(w.gamma, w.beta, w.lam, w.Omega)
-    k = 4
-    ref = O.pcg_ground_state(oplan, oprm, W.initial_guess(w), O.PcgOptions(max_iter=k))
-    plan, psi, res = _run_pair(lib, w, k)
-    assert res["iters"] == k
-    for a, b in zip(res["log"], ref.log):
-        assert abs(a["E"] - b["E"]) <= 1e-10 * abs(b["E"])
-        assert abs(a["residual"] - b["residual"]) <= 1e-8 * b["residual"]
-        assert a["halvings"] == b.get("halvings", a["halvings"])
-    phi = host(psi)
-    assert rel2(phi, ref.phi) <= 1e-9
-
-
 def test_pcg_harmonic_oscillator(lib):
     N, L = (32, 32, 32), (8.0, 8.0, 4.0)
     plan = lib.Plan(N, L, (0, 0, 1))
