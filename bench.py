@@ -66,7 +66,8 @@ def parse():
                     help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
-                                               "profiling_overhead", "polish_df32", "fp64_peak"],
+                                               "profiling_overhead", "polish_df32", "fp64_peak", "iterations",
+                                               "virial_vs_tol", "engines"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture, or one of the "
                          "timings quoted in the design notes, and exit")
     a = ap.parse_args()
@@ -590,6 +591,109 @@ def timing_case(case: str):
         plan.close()
 
 
+def study_case(case: str):
+    """iterations: Algorithm 1 (binary64, one level, guess (d), residual 1e-8)
+    on Example 3.1 (Cases I and II, Omega = 0.2 and 0.6) at 32^3 ... 256^3,
+    on the 32x32x16 workload and on the bench box at 64x64x16 and
+    128x128x32: iterations and the step-control events per run.
+    virial_vs_tol: Example 3.1 Case II, Omega = 0.8 by Algorithm 2 (32^3,
+    64^3, 128^3 in binary64 from guess (a)), then the 128^3 solve continued
+    to residual 1e-9 ... 1e-12: |I| and the energy terms at each."""
+    import numpy as np
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+
+    def events(log):
+        steps = log[:-1]
+        return dict(resets=sum(int(e["reset_to_sd"]) for e in steps), t_default=sum(int(e["curvature"] <= 0) for e in steps),
+                    halvings=sum(e["halvings"] for e in steps), beta_zero=sum(int(e["beta_cg"] == 0.0) for e in steps))
+
+    def single(name, N, L, gamma, beta, lam, n, Om, psi0, max_iter=20000):
+        plan = B.Plan(N, L, n)
+        psi = torch.from_numpy(psi0).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = plan.pcg_ground_state(B.make_params(gamma, beta, lam, Om), psi, tol_residual=TOL, max_iter=max_iter,
+                                  log_capacity=max_iter + 2)
+        torch.cuda.synchronize()
+        out = dict(case=case, name=name, grid=list(N), Omega=Om, status=r["status_name"], iters=r["iters"], E=r["E"],
+                   virial=r["virial"], seconds=round(time.perf_counter() - t0, 3))
+        out.update(events(r["log"]))
+        print(json.dumps(out), flush=True)
+        plan.close()
+
+    if case == "iterations":
+        for cs, gamma, L in (("I", (1.0, 1.0, 1.0), (16.0, 16.0, 16.0)), ("II", (1.0, 2.0, 10.0), (16.0, 16.0, 10.0))):
+            for Om in (0.2, 0.6):
+                for m in (32, 64, 128, 256):
+                    N = (m, m, m)
+                    single(f"example3.1_case{cs}", N, L, gamma, 100.0, 80.0, (0.0, 0.0, 1.0), Om,
+                           W.guess_phi_d(N, L, gamma, Om))
+        w1 = W.CONFIGS["cfg1_32x32x16"]
+        single(w1.name, w1.N, w1.L, w1.gamma, w1.beta, w1.lam, w1.n, w1.Omega, W.initial_guess(w1))
+        w3 = W.CONFIGS[WORKLOAD]
+        for N in ((64, 64, 16), (128, 128, 32)):
+            single(w3.name + "_box", N, w3.L, w3.gamma, w3.beta, w3.lam, w3.n, w3.Omega,
+                   W.initial_guess(W.with_grid(w3, N)))
+        return
+    gamma, L = (1.0, 2.0, 10.0), (16.0, 16.0, 10.0)
+    grids = [(m, m, m) for m in (32, 64, 128)]
+    plans = [B.Plan(N, L, (0.0, 0.0, 1.0)) for N in grids]
+    x, y, z = W.mesh(grids[0], L)
+    g = np.exp(-(x * x + y * y + z * z) / 2).astype(np.complex128) * np.ones((32, 32, 32))
+    psis = [torch.from_numpy(g).cuda()] + [torch.empty(p.shape, dtype=torch.complex128, device="cuda")
+                                           for p in plans[1:]]
+    prm = B.make_params(gamma, 100.0, 80.0, 0.8)
+    res = B.pcg_ground_state_mg(plans, prm, psis, tol_residual=TOL, max_iter=20000)
+    parts = ("E_kin", "E_pot", "E_int", "E_dip", "E_rot")
+    print(json.dumps(dict(case=case, tol=TOL, iters=[r["iters"] for r in res], E=res[-1]["E"],
+                          virial=res[-1]["virial"], **{k: res[-1][k] for k in parts})), flush=True)
+    for tol in (1e-9, 1e-10, 1e-11, 1e-12):
+        r = plans[-1].pcg_ground_state(prm, psis[-1], tol_residual=tol, max_iter=20000, resume=True)
+        print(json.dumps(dict(case=case, tol=tol, iters=r["iters"], E=r["E"], virial=r["virial"],
+                              residual=r["residual"], **{k: r[k] for k in parts})), flush=True)
+    for p in plans:
+        p.close()
+
+
+def engines_case():
+    """engines: the FFT engines on the grids of the uneven-grid sweep
+    (edge e in-plane, e/4 along z, box of the sweep): stand-alone ATKM and
+    H phi, binary64 and FP32, with the default engine choice and with every
+    non-power-of-two length on the generic engine (ATKM_PLAN_GENERIC_FFT);
+    CUDA events around 20 back-to-back calls, one JSON line per grid."""
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+    for e in (72, 80, 96, 120, 144, 160, 192):
+        N = (e, e, e // 4)
+        L = (16.0, 16.0, math.sqrt(64.0 / 20.0))
+        psi = torch.from_numpy(W.guess_phi_d(N, L, (1.0, 1.0, 20.0), 0.7)).cuda()
+        prm = B.make_params((1.0, 1.0, 20.0), 200.0, 60.0, 0.7)
+        row = {"case": "engines", "grid": list(N)}
+        for label, gen in (("default", False), ("generic", True)):
+            plan = B.Plan(N, L, (0.0, 0.0, 1.0), f32=True, generic_fft=gen)
+            Phi = plan.dipolar_potential_from_psi(psi)
+            Hf = torch.empty_like(psi)
+            calls = {"atkm_f64": lambda: plan.dipolar_potential_from_psi(psi, out=Phi),
+                     "atkm_f32": lambda: plan.dipolar_potential_from_psi(psi, out=Phi, f32=True),
+                     "H_f64": lambda: plan.apply_H(prm, psi, psi, Phi, out=Hf)}
+            for name, fn in calls.items():
+                for _ in range(3):
+                    fn()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(20):
+                    fn()
+                b.record()
+                torch.cuda.synchronize()
+                row[f"{name}_{label}_ms"] = round(a.elapsed_time(b) / 20, 4)
+            plan.close()
+        print(json.dumps(row), flush=True)
+
+
 def profile_case(case: str):
     """Small fixed workloads on the bench grid for ncu captures (about 1 GB of
     device memory): two ATKM evaluations, or three PCG iterations; or a
@@ -597,6 +701,12 @@ def profile_case(case: str):
     the roofline denominator of the binary64 passes, one JSON line)."""
     if case in ("profiling_overhead", "polish_df32"):
         timing_case(case)
+        return
+    if case in ("iterations", "virial_vs_tol"):
+        study_case(case)
+        return
+    if case == "engines":
+        engines_case()
         return
     if case == "fp64_peak":
         from paper_2603_05194_gb300 import binding as B

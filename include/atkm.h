@@ -52,6 +52,11 @@ typedef struct atkm_plan atkm_plan;
 #define ATKM_PLAN_F64 0u   /* FP64 workspaces (always present)                  */
 #define ATKM_PLAN_F32 1u   /* also allocate complex64 workspaces for the _f32 calls */
 #define ATKM_PLAN_DF32 2u  /* also keep a double-word copy of U0 for the _df32 calls  */
+#define ATKM_PLAN_GENERIC_FFT 4u  /* lengths that are not powers of two run on the generic
+                                     shared-memory FFT engine also where the mixed-radix
+                                     register engine covers them (3 * 2^a and 5 * 2^a,
+                                     20 <= L <= 384); for comparisons, same results to
+                                     rounding                                            */
 
 /*
  * atkm_plan_create -- grid, box, dipole axis; precomputes the truncated-kernel
@@ -253,7 +258,7 @@ typedef struct atkm_pcg_opts {
                            from its global timer, in the device-driven loop); the
                            state reached is returned and can be resumed          */
   int f32_window;       /* precision forms: FP32-phase iterations without halving the
-                           best FP32 residual before the hand-over (0: 400)      */
+                           best FP32 residual before the hand-over (0: 50)       */
 } atkm_pcg_opts;
 
 /* One record per iteration n (values at phi_n; step fields describe n -> n+1). */
@@ -377,11 +382,14 @@ int atkm_guess_net_train_step(atkm_guess_net* net, int batch, const float* feats
                               float lr, float* loss, void* stream);
 /* One training step as atkm_guess_net_train_step, with every GEMM bracketed by
  * CUDA events on `stream`: *gemm_ms = their summed time, *step_ms = the whole
- * step, *gemm_calls = the GEMMs timed (host outputs; synchronises `stream`).
+ * step, *gemm_calls = the GEMMs timed, each_ms[i] (if not NULL, up to
+ * each_cap entries) the time of GEMM i in launch order: the five forward
+ * layers, then per layer from the last the weight gradient and (but for the
+ * first layer) the input gradient (host outputs; synchronises `stream`).
  * Measurement support; the paper has no counterpart. */
 int atkm_guess_net_profile_step(atkm_guess_net* net, int batch, const float* feats, const double* targets,
                                 float lr, float* loss, double* gemm_ms, double* step_ms, int* gemm_calls,
-                                void* stream);
+                                double* each_ms, int each_cap, void* stream);
 
 /*
  * atkm_inner_products_noalloc -- out[i] = hvol * Re(sum_j u_i[j] conj(v_i[j]))

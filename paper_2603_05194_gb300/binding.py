@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED_SIZE", 3: "ERR_OOM", 
                 5: "NOT_CONVERGED", 6: "STAGNATED", 7: "ERR_NAN", 8: "ERR_TIMEOUT"}
 ATKM_PLAN_F32 = 1
 ATKM_PLAN_DF32 = 2
+ATKM_PLAN_GENERIC_FFT = 4
 PRECISION_F64 = 0
 PRECISION_F32_F64 = 1
 PRECISION_F32_SPLIT = 2
@@ -114,7 +115,8 @@ def load_library(path: str = LIB_PATH):
         "atkm_guess_net_forward": (ip, [vp, C.c_int, vp, vp, vp]),
         "atkm_guess_net_grad": (ip, [vp, C.c_int, vp, vp, vp, vp, vp]),
         "atkm_guess_net_train_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, vp]),
-        "atkm_guess_net_profile_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, dp, dp, C.POINTER(C.c_int), vp]),
+        "atkm_guess_net_profile_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, dp, dp, C.POINTER(C.c_int), dp,
+                                             C.c_int, vp]),
         "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
         "atkm_measure_fp64_fma": (ip, [C.c_int, C.c_int, C.c_int, dp, vp]),
         "atkm_launch_count": (C.c_ulonglong, []),
@@ -291,11 +293,13 @@ class GuessNet:
         _ptr(targets, torch.complex128, (B,) + GUESS_SHAPE, "targets")
         loss = torch.empty(1, dtype=torch.float32, device="cuda")
         g, t, n = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
+        each = (C.c_double * 16)()
         self._check(self._lib.atkm_guess_net_profile_step(self._h, B, C.c_void_p(feats.data_ptr()),
                                                           C.c_void_p(targets.data_ptr()), C.c_float(lr),
                                                           C.c_void_p(loss.data_ptr()), C.byref(g), C.byref(t),
-                                                          C.byref(n), _stream(stream)))
-        return {"gemm_ms": g.value, "step_ms": t.value, "gemm_calls": n.value, "loss": float(loss.item())}
+                                                          C.byref(n), each, 16, _stream(stream)))
+        return {"gemm_ms": g.value, "step_ms": t.value, "gemm_calls": n.value, "loss": float(loss.item()),
+                "each_ms": [each[i] for i in range(min(n.value, 16))]}
 
 
 def measure_fp64_fma(blocks_per_sm=8, iters=4096, repeats=5, stream=None) -> float:
@@ -340,7 +344,7 @@ def make_params(gamma, beta, lam, Omega) -> Params:
 class Plan:
     """Owning handle of an atkm_plan (grid, box, dipole axis, multiplier)."""
 
-    def __init__(self, N, L, n, f32: bool = False, stream=None, df32: bool = False):
+    def __init__(self, N, L, n, f32: bool = False, stream=None, df32: bool = False, generic_fft: bool = False):
         lib = load_library()
         self.N = tuple(int(v) for v in N)
         self.L = tuple(float(v) for v in L)
@@ -350,7 +354,8 @@ class Plan:
         Na = (C.c_int * 3)(*self.N)
         La = (C.c_double * 3)(*self.L)
         na = (C.c_double * 3)(*self.n)
-        flags = (ATKM_PLAN_F32 if f32 else 0) | (ATKM_PLAN_DF32 if df32 else 0)
+        flags = (ATKM_PLAN_F32 if f32 else 0) | (ATKM_PLAN_DF32 if df32 else 0) | \
+            (ATKM_PLAN_GENERIC_FFT if generic_fft else 0)
         code = lib.atkm_plan_create(C.byref(self._h), Na, La, na, flags, _stream(stream))
         if code != ATKM_OK:
             raise AtkmError(code, lib.atkm_last_error_string(None).decode())

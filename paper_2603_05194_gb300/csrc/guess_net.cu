@@ -138,6 +138,116 @@ k_gemm_bf16(const float* __restrict__ A, long sam, long sak, const float* __rest
       }
 }
 
+// ---- Skinny contractions.  Every layer but the MLP's second is either a
+// product whose output rows each need only K x N <= 4096 weights (the
+// transposed convolutions and their input gradients: K or N is 8 to 128) or a
+// weight gradient with M x N <= 4096 outputs summed over K = 8192 ... 524288
+// rows.  Both are bound by memory, not by multiply-adds, so they run on the
+// CUDA cores with the operands rounded to BF16 exactly as the tensor-core
+// path stages them and FP32 products and sums.
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+constexpr int kRowsThreads = 256;
+
+// C[M x N] = A[M x K] B[K x N], A rows contiguous (A(m,k) = A[m*sam + k]):
+// each thread forms NT consecutive outputs of one row; B (K x N, any
+// strides) is staged in shared memory.
+template <int NT>
+__device__ __forceinline__ void gemm_rows(const float* __restrict__ A, long sam, const float* __restrict__ Bm, long sbk,
+                                          long sbn, float* __restrict__ C, int ldc, int M, int N, int K) {
+  extern __shared__ float bsm[];  // [K][N]
+  for (int i = threadIdx.x; i < K * N; i += kRowsThreads) {
+    const int k = i / N, n = i - k * N;
+    bsm[i] = bf16r(Bm[(long)k * sbk + (long)n * sbn]);
+  }
+  __syncthreads();
+  const int chunks = N / NT;
+  const long tid = (long)blockIdx.x * kRowsThreads + threadIdx.x;
+  const long row = tid / chunks;
+  const int c = (int)(tid - row * chunks);
+  if (row >= M) return;
+  float acc[NT];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n] = 0.f;
+  const float* a = A + row * sam;
+  for (int k = 0; k < K; ++k) {
+    const float av = bf16r(__ldg(a + k));
+    const float* b = bsm + k * N + c * NT;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n] = fmaf(av, b[n], acc[n]);
+  }
+  float* out = C + row * ldc + c * NT;
+#pragma unroll
+  for (int n = 0; n < NT; ++n) out[n] = acc[n];
+}
+__global__ void __launch_bounds__(kRowsThreads)
+k_gemm_rows8(const float* __restrict__ A, long sam, const float* __restrict__ Bm, long sbk, long sbn,
+             float* __restrict__ C, int ldc, int M, int N, int K) {
+  gemm_rows<8>(A, sam, Bm, sbk, sbn, C, ldc, M, N, K);
+}
+__global__ void __launch_bounds__(kRowsThreads)
+k_gemm_rows16(const float* __restrict__ A, long sam, const float* __restrict__ Bm, long sbk, long sbn,
+              float* __restrict__ C, int ldc, int M, int N, int K) {
+  gemm_rows<16>(A, sam, Bm, sbk, sbn, C, ldc, M, N, K);
+}
+
+// C[M x N] += X^T Y over rows k of X (K x M, rows ldx apart) and Y (K x N,
+// rows ldy apart): each CTA stages blocks of kTnRows rows in shared memory
+// and sums its rows into per-thread outputs, then adds them into C (zeroed
+// by the caller) atomically.
+constexpr int kTnRows = 32;
+__global__ void __launch_bounds__(kRowsThreads)
+k_gemm_tn(const float* __restrict__ X, long ldx, const float* __restrict__ Y, long ldy, float* __restrict__ C,
+          int ldc, int M, int N, long K, long rows_per_cta) {
+  extern __shared__ float tsm[];  // [kTnRows][M] then [kTnRows][N]
+  float* xs = tsm;
+  float* ys = tsm + kTnRows * M;
+  const int MN = M * N;
+  const int P = MN >= kRowsThreads ? 1 : kRowsThreads / MN;  // row phases
+  const int O = MN >= kRowsThreads ? (MN + kRowsThreads - 1) / kRowsThreads : 1;  // outputs a thread
+  const int o0 = MN >= kRowsThreads ? threadIdx.x : (int)(threadIdx.x % MN);
+  const int ph = MN >= kRowsThreads ? 0 : (int)(threadIdx.x / MN);
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  const long k0 = (long)blockIdx.x * rows_per_cta, k1 = k0 + rows_per_cta < K ? k0 + rows_per_cta : K;
+  for (long kb = k0; kb < k1; kb += kTnRows) {
+    const int nr = (int)(k1 - kb < kTnRows ? k1 - kb : kTnRows);
+    for (int i = threadIdx.x; i < nr * M; i += kRowsThreads) {
+      const int r = i / M, m = i - r * M;
+      xs[i] = bf16r(X[(kb + r) * ldx + m]);
+    }
+    for (int i = threadIdx.x; i < nr * N; i += kRowsThreads) {
+      const int r = i / N, n = i - r * N;
+      ys[i] = bf16r(Y[(kb + r) * ldy + n]);
+    }
+    __syncthreads();
+    if (ph < P) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j >= O) break;
+        const int o = o0 + j * kRowsThreads;
+        if (o >= MN) break;
+        const int m = o / N, n = o - m * N;
+        float a = acc[j];
+        for (int r = ph; r < nr; r += P) a = fmaf(xs[r * M + m], ys[r * N + n], a);
+        acc[j] = a;
+      }
+    }
+    __syncthreads();
+  }
+  if (ph < P) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j >= O) break;
+      const int o = o0 + j * kRowsThreads;
+      if (o >= MN) break;
+      const int m = o / N, n = o - m * N;
+      atomicAdd(C + (long)m * ldc + n, acc[j]);
+    }
+  }
+}
+
 // ------------------------------------------------------------- elementwise
 // y = act(x + b[col % cb]) in place (act = relu when relu != 0).
 __global__ void k_bias_act(float* __restrict__ x, const float* __restrict__ b, long rows, int cols, int cb, int relu) {
@@ -398,6 +508,32 @@ cudaError_t gemm(const float* A, long sam, long sak, const float* Bm, long sbk, 
 
 cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc,
                         int M, int N, int K, cudaStream_t st, bool split_k) {
+  // row-local products: the output rows need only K x N <= 4096 weights
+  if (sak == 1 && (long)K * N <= 4096 && N % 8 == 0 && M >= 1024) {
+    const int nt = N % 16 == 0 ? 16 : 8;
+    const long threads = (long)M * (N / nt);
+    const int blocks = (int)((threads + kRowsThreads - 1) / kRowsThreads);
+    const size_t sm = (size_t)K * N * sizeof(float);
+    if (nt == 16)
+      k_gemm_rows16<<<blocks, kRowsThreads, sm, st>>>(A, sam, Bm, sbk, sbn, C, ldc, M, N, K);
+    else
+      k_gemm_rows8<<<blocks, kRowsThreads, sm, st>>>(A, sam, Bm, sbk, sbn, C, ldc, M, N, K);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  // weight gradients: M x N <= 4096 outputs summed over many rows
+  if (split_k && sam == 1 && sbn == 1 && (long)M * N <= 4096 && K >= 1024) {
+    cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * ldc * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const int nsm = std::max(device_sm_count(), 1);
+    long ctas = std::min<long>((long)nsm * 4, ((long)K + kTnRows - 1) / kTnRows);
+    const long rows = ((long)K + ctas - 1) / ctas;
+    ctas = ((long)K + rows - 1) / rows;
+    const size_t sm = (size_t)kTnRows * (M + N) * sizeof(float);
+    k_gemm_tn<<<(int)ctas, kRowsThreads, sm, st>>>(A, sak, Bm, sbk, C, ldc, M, N, (long)K, rows);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   int splits = 1;
   const int tiles = ((M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
   const int nsm = std::max(device_sm_count(), 1);
@@ -465,7 +601,7 @@ cudaError_t net_backward(atkm_guess_net* n, int B, const double* targets, float*
   // MLP2 (no activation on z)
   if ((e = gemm(n->h1, 1, kH, n->dz, kZ, 1, g + kL.W2, kZ, kH, kZ, B, st, true))) return e;
   k_bias_grad<<<dim3(kZ, 1), 256, 0, st>>>(n->dz, g + kL.b2, B, kZ, kZ);
-  if ((e = gemm(n->dz, kZ, 1, w + kL.W2, 1, kZ, n->dh1, kH, B, kH, kZ, st, false))) return e;
+  if ((e = gemm(n->dz, kZ, 1, w + kL.W2, 1, kZ, n->dh1, kH, B, kH, kZ, st, true))) return e;
   k_relu_back<<<ew_grid((long)B * kH), 256, 0, st>>>(n->dh1, n->h1, (long)B * kH);
   // MLP1
   if ((e = gemm(n->fpad, 1, kFpad, n->dh1, kH, 1, g + kL.W1, kH, kFpad, kH, B, st, true))) return e;
@@ -589,7 +725,8 @@ int atkm_guess_net_train_step(atkm_guess_net* n, int batch, const float* feats, 
  * CUDA events: *gemm_ms the summed GEMM time, *step_ms the whole step, both
  * on `stream`, which this call synchronises. */
 int atkm_guess_net_profile_step(atkm_guess_net* n, int batch, const float* feats, const double* targets, float lr,
-                                float* loss, double* gemm_ms, double* step_ms, int* gemm_calls, void* stream) {
+                                float* loss, double* gemm_ms, double* step_ms, int* gemm_calls, double* each_ms,
+                                int each_cap, void* stream) {
   if (!gemm_ms || !step_ms || !gemm_calls) return net_fail(n, ATKM_ERR_ARG, "atkm_guess_net_profile_step: NULL output");
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -607,9 +744,12 @@ int atkm_guess_net_profile_step(atkm_guess_net* n, int batch, const float* feats
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   double g = 0.0;
   float ms = 0.0f;
+  int i = 0;
   for (auto& pr : timer.ev) {
     float t = 0.0f;
     if (e == cudaSuccess && cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) g += t;
+    if (each_ms && i < each_cap) each_ms[i] = t;
+    ++i;
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }

@@ -473,13 +473,24 @@ struct PassGrid {
   dim3 grid;
   int T;
   bool fast;
+  bool mix;  // the mixed-radix register engine (mix.cuh)
 };
 
+bool mix_len(int L);
+
 // LM passes: `lines` lines; strided passes: `X` columns x `outer` outer indices.
-template <typename R> inline PassGrid pass_grid(int L, bool LM, long lines, int X, int outer) {
+// Engine: the power-of-two register engine, else the mixed-radix register
+// engine for 3 * 2^a (FP32 and binary64) and 5 * 2^a (FP32; in binary64 its
+// 20 complex doubles a thread make it slower than the generic engine,
+// measured), not with ATKM_PLAN_GENERIC_FFT, else the generic shared-memory
+// engine.
+template <typename R> inline PassGrid pass_grid(const atkm_plan* p, int L, bool LM, long lines, int X, int outer) {
   PassGrid pg;
   pg.fast = fast_len(L);
+  pg.mix = !pg.fast && !std::is_same<R, df>::value && !(p->flags & ATKM_PLAN_GENERIC_FFT) && mix_len(L) &&
+           !(std::is_same<R, double>::value && L % 5 == 0);
   if (pg.fast) pg.T = kFastElems / L;
+  else if (pg.mix) pg.T = kThreads / (L / (L % 3 == 0 ? 12 : 20));
   else pg.T = LM ? gen_lm_tile<R>(L, lines) : gen_col_tile<R>(L, X, outer);
   if (LM) pg.grid = dim3(ceil_div_l(lines, pg.T), 1, 1);
   else pg.grid = dim3(ceil_div_l(X, pg.T), outer, 1);
@@ -517,8 +528,38 @@ inline cudaError_t launch_fast_L(const Op& op, const FftLen& f, const PassGrid& 
   return cudaGetLastError();
 }
 
+}  // namespace atkm
+#include "mix.cuh"
+namespace atkm {
+
 template <typename R, class Op>
 inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (pg.mix) {
+      switch (f.L) {
+        case 20: return launch_mix_L<R, 20>(op, f, pg, st);
+        case 24: return launch_mix_L<R, 24>(op, f, pg, st);
+        case 40: return launch_mix_L<R, 40>(op, f, pg, st);
+        case 48: return launch_mix_L<R, 48>(op, f, pg, st);
+        case 80: return launch_mix_L<R, 80>(op, f, pg, st);
+        case 96: return launch_mix_L<R, 96>(op, f, pg, st);
+        case 160: return launch_mix_L<R, 160>(op, f, pg, st);
+        case 192: return launch_mix_L<R, 192>(op, f, pg, st);
+        case 320: return launch_mix_L<R, 320>(op, f, pg, st);
+        default: return launch_mix_L<R, 384>(op, f, pg, st);
+      }
+    }
+  } else if constexpr (std::is_same<R, double>::value) {
+    if (pg.mix) {
+      switch (f.L) {
+        case 24: return launch_mix_L<R, 24>(op, f, pg, st);
+        case 48: return launch_mix_L<R, 48>(op, f, pg, st);
+        case 96: return launch_mix_L<R, 96>(op, f, pg, st);
+        case 192: return launch_mix_L<R, 192>(op, f, pg, st);
+        default: return launch_mix_L<R, 384>(op, f, pg, st);
+      }
+    }
+  }
   if (pg.fast) {
     switch (f.L) {
       case 16: return launch_fast_L<R, 16>(op, f, pg, st);

@@ -98,7 +98,7 @@ cudaError_t atkm_pass_xf(atkm_plan* p, int mode, const double* a, const double* 
   const Geo& g = *x.g;
   if (!x.W1) return cudaErrorInvalidValue;
   const double inb = mode == SRC_RHO ? 8.0 : (mode == SRC_PSI ? 16.0 : 32.0);
-  const PassGrid gx = pass_grid<R>(g.Nx, true, x.nl, 0, 0);
+  const PassGrid gx = pass_grid<R>(p, g.Nx, true, x.nl, 0, 0);
   const char* nx = nm<R>("atkm_x_fwd_f64", "atkm_x_fwd_f32", "atkm_x_fwd_df");
   if (mode == SRC_RHO) {
     OpAtkmXF<R, SRC_RHO> op; op.a = a; op.b = b; op.W1 = x.W1; op.twM = x.twM; op.c = x.c; op.XS = g.XS;
@@ -119,7 +119,7 @@ cudaError_t atkm_pass_yf(atkm_plan* p, int, const double*, const double*, double
   const AtkmCtx<R> x = atkm_ctx<R>(p);
   const Geo& g = *x.g;
   if (!x.W1 || !x.W2) return cudaErrorInvalidValue;
-  const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
+  const PassGrid gy = pass_grid<R>(p, g.My, false, 0, g.Xh, g.Nz);
   OpAtkmYF<R> op; op.W1 = x.W1; op.W2 = x.W2; op.c = x.c; op.XS = g.XS;
   ATKM_RUN(nm<R>("atkm_y_fwd_f64", "atkm_y_fwd_f32", "atkm_y_fwd_df"), 3 * x.H1 * x.s, x.fy, op, p->fM[1], gy);
   return cudaSuccess;
@@ -134,7 +134,7 @@ cudaError_t atkm_pass_z(atkm_plan* p, int, const double*, const double*, double*
   OpAtkmZ<R> op; op.W2 = x.W2; op.K = x.K; op.U0 = x.K; op.c = x.c; op.XS = g.XS;
   op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
   op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
-  const PassGrid pg = pass_grid<R>(g.Mz, false, 0, g.Xh, g.My);
+  const PassGrid pg = pass_grid<R>(p, g.Mz, false, 0, g.Xh, g.My);
   ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * x.H1 * x.s + x.kb, x.fz, op, p->fM[2], pg);
   return cudaSuccess;
 }
@@ -145,7 +145,7 @@ cudaError_t atkm_pass_yi(atkm_plan* p, int, const double*, const double*, double
   const AtkmCtx<R> x = atkm_ctx<R>(p);
   const Geo& g = *x.g;
   if (!x.W1 || !x.W2) return cudaErrorInvalidValue;
-  const PassGrid gy = pass_grid<R>(g.My, false, 0, g.Xh, g.Nz);
+  const PassGrid gy = pass_grid<R>(p, g.My, false, 0, g.Xh, g.Nz);
   OpAtkmYI<R> op; op.W2 = x.W2; op.W1 = x.W1; op.c = x.c; op.XS = g.XS;
   ATKM_RUN(nm<R>("atkm_y_inv_f64", "atkm_y_inv_f32", "atkm_y_inv_df"), 3 * x.H1 * x.s, x.fy, op, p->fM[1], gy);
   return cudaSuccess;
@@ -157,7 +157,7 @@ cudaError_t atkm_pass_xi(atkm_plan* p, int, const double*, const double*, double
   const AtkmCtx<R> x = atkm_ctx<R>(p);
   const Geo& g = *x.g;
   if (!x.W1) return cudaErrorInvalidValue;
-  const PassGrid gx = pass_grid<R>(g.Nx, true, x.nl, 0, 0);
+  const PassGrid gx = pass_grid<R>(p, g.Nx, true, x.nl, 0, 0);
   OpAtkmXI<R> op; op.W1 = x.W1; op.phi = phi; op.twM = x.twM; op.c = x.c; op.XS = g.XS;
   ATKM_RUN(nm<R>("atkm_x_inv_f64", "atkm_x_inv_f32", "atkm_x_inv_df"), x.H1 * x.s + 8 * x.N, x.fx, op, p->fN[0],
            gx);
@@ -195,7 +195,7 @@ cudaError_t h_pass_x(atkm_plan* p, const Phys& ph, const double* f, const double
   (void)pin; (void)out; (void)nl; (void)pr; (void)e;
   // x
   {
-    const PassGrid pg = pass_grid<R>(g.Nx, true, nl, 0, 0);
+    const PassGrid pg = pass_grid<R>(p, g.Nx, true, nl, 0, 0);
     const double fl = 2.0 * nl * fftflops(g.Nx);
     const char* n = nm<R>("H_x_f64", "H_x_f32", "H_x_df");
     if (red) {
@@ -229,7 +229,7 @@ cudaError_t h_pass_y(atkm_plan* p, const Phys& ph, const double* f, const double
   (void)pin; (void)out; (void)nl; (void)pr; (void)e;
   // y
   {
-    const PassGrid pg = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
+    const PassGrid pg = pass_grid<R>(p, g.Ny, false, 0, g.Nx, g.Nz);
     const double fl = 2.0 * g.Nz * g.Nx * fftflops(g.Ny);
     const char* n = nm<R>("H_y_f64", "H_y_f32", "H_y_df");
     if (red) {
@@ -263,7 +263,7 @@ cudaError_t h_pass_z(atkm_plan* p, const Phys& ph, const double* f, const double
   (void)pin; (void)out; (void)nl; (void)pr; (void)e;
   // z + pointwise
   {
-    const PassGrid pg = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
+    const PassGrid pg = pass_grid<R>(p, g.Nz, false, 0, g.Nx, g.Ny);
     const double fl = 2.0 * g.Ny * g.Nx * fftflops(g.Nz);
     const char* n = nm<R>("H_z_f64", "H_z_f32", "H_z_df");
     if (red) {
@@ -303,9 +303,9 @@ cudaError_t launch_precond(atkm_plan* p, const Phys& ph, const double* alpha_dev
   const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
   const long nl = (long)g.Nz * g.Ny;
   const double fx = (double)nl * fftflops(g.Nx), fy = (double)g.Nz * g.Nx * fftflops(g.Ny);
-  const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
-  const PassGrid gy = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
-  const PassGrid gz = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
+  const PassGrid gx = pass_grid<R>(p, g.Nx, true, nl, 0, 0);
+  const PassGrid gy = pass_grid<R>(p, g.Ny, false, 0, g.Nx, g.Nz);
+  const PassGrid gz = pass_grid<R>(p, g.Nz, false, 0, g.Nx, g.Ny);
   {
     OpPXF<R> op; op.r = reinterpret_cast<const double2*>(r); op.phi = reinterpret_cast<const double2*>(phi);
     op.Phi = Phi; op.Wk = Wk; op.c = c; op.ph = pr; op.alpha = alpha_dev;
@@ -343,9 +343,9 @@ cudaError_t launch_cfft3(atkm_plan* p, cx<R>* buf, int sign, cudaStream_t st) {
   const Cst<R> c = make_cst<R>(g);
   const double N = (double)g.Nx * g.Ny * g.Nz, s = (double)sizeof(cx<R>);
   const long nl = (long)g.Nz * g.Ny;
-  const PassGrid gx = pass_grid<R>(g.Nx, true, nl, 0, 0);
-  const PassGrid gy = pass_grid<R>(g.Ny, false, 0, g.Nx, g.Nz);
-  const PassGrid gz = pass_grid<R>(g.Nz, false, 0, g.Nx, g.Ny);
+  const PassGrid gx = pass_grid<R>(p, g.Nx, true, nl, 0, 0);
+  const PassGrid gy = pass_grid<R>(p, g.Ny, false, 0, g.Nx, g.Nz);
+  const PassGrid gz = pass_grid<R>(p, g.Nz, false, 0, g.Nx, g.Ny);
   const double fx = (double)nl * fftflops(g.Nx), fy = (double)g.Nz * g.Nx * fftflops(g.Ny),
                fz = (double)g.Ny * g.Nx * fftflops(g.Nz);
   if (sign < 0) {

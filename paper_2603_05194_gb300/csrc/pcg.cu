@@ -494,8 +494,11 @@ __global__ void k_c_reset_state(Ctl* c, int have_E, int force_sd, int clear_prev
 // loop is also bounded by a guard counter derived from max_iter and
 // max_halvings, so a graph launch always ends.
 // FP32 phase stagnation: no halving of the best FP32 residual for this many
-// iterations (opts.f32_window, this when 0) hands over to FP64.
-constexpr int kF32Window = 400;
+// iterations (opts.f32_window, this when 0) hands over to FP64.  A long window
+// wastes FP32 iterations at the FP32 residual floor (400 cost the finest level
+// of a 256^3 multigrid solve 350 of them); 50 keeps the long bulk phases of
+// fast-rotating states within about 10% of their time.
+constexpr int kF32Window = 50;
 
 struct LoopInit {
   int n, max_iter, max_halv, caps, f32, log_cap, q, f32_window;

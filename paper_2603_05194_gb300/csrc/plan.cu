@@ -438,7 +438,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   if (!isfinite(nn) || fabs(nn - 1.0) > 1e-12)
     return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: dipole axis must be a unit vector (| |n|-1 | <= 1e-12)");
-  if (flags & ~(unsigned)(ATKM_PLAN_F32 | ATKM_PLAN_DF32))
+  if (flags & ~(unsigned)(ATKM_PLAN_F32 | ATKM_PLAN_DF32 | ATKM_PLAN_GENERIC_FFT))
     return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: unknown flags");
 
   cudaStream_t st = (cudaStream_t)stream;

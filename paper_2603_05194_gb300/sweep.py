@@ -1,11 +1,11 @@
 """Batched sweep of independent ground-state problems on uneven grids.
 
 Every instance is its own Algorithm 1 run (own plan, own multiplier K, own
-state); pcg_ground_state_batched runs them concurrently, each on its own
-stream with graph-captured iterations, and the host processes each instance as
-soon as its last phase has finished.  This module times that call against the
-same instances solved one after another, and runs the sweep to the residual
-tolerance.  It only orders calls and keeps the books.
+state); pcg_ground_state_batched builds all of them into one CUDA graph and
+launches it once.  This module times that call against the same instances
+solved one after another, and runs the sweep to the residual tolerance (in
+one launch, double-word split form), optionally against each instance solved
+alone in binary64.  It only orders calls and keeps the books.
 """
 from __future__ import annotations
 
@@ -28,7 +28,7 @@ def _timed(fn):
 
 
 def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PRECISION_F32_F64, B.PRECISION_F64),
-        log=print):
+        log=print, reference=False):
     plans = [B.Plan(p.N, p.L, p.n, f32=True, df32=True) for p in problems]
     prms = [B.make_params(p.gamma, p.beta, p.lam, p.Omega) for p in problems]
 
@@ -53,14 +53,34 @@ def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PR
             log(f"{name}: {iters} iterations x {len(problems)} instances: batched {tb:.3f} s, "
                 f"one by one {ts:.3f} s ({ts / tb:.2f}x)")
         if full_iters > 0:
+            # the sweep to the tolerance: all instances in one graph launch
+            # (double-word split form) against each instance alone in binary64
             ps = psis()
             res, t = _timed(lambda: B.pcg_ground_state_batched(plans, prms, ps, max_iter=full_iters, tol_residual=tol,
                                                                precision=B.PRECISION_DF32_SPLIT))
             st = collections.Counter(r["status_name"] for r in res)
             out["full"] = dict(tol=tol, max_iter=full_iters, seconds=t, statuses=dict(st),
                                iters=[r["iters"] for r in res], residual=[r["residual"] for r in res],
-                               E=[r["E"] for r in res])
-            log(f"sweep to {tol:g} (double-word split form, at most {full_iters} iterations): {t:.1f} s, {dict(st)}")
+                               E=[r["E"] for r in res], device_loop=all(r["device_loop"] for r in res))
+            log(f"sweep to {tol:g} (one launch, double-word split form, at most {full_iters} iterations): "
+                f"{t:.1f} s, {dict(st)}")
+            if reference:
+                ps = psis()
+                ref, tr = _timed(lambda: [pl.pcg_ground_state(pr, p, max_iter=full_iters, tol_residual=tol,
+                                                              precision=B.PRECISION_F64)
+                                          for pl, pr, p in zip(plans, prms, ps)])
+                sr = collections.Counter(r["status_name"] for r in ref)
+                both = [(a, b) for a, b in zip(res, ref) if a["status"] == B.ATKM_OK and b["status"] == B.ATKM_OK]
+                dE = [(a["E"] - b["E"]) / abs(b["E"]) for a, b in both]
+                out["reference_f64_one_by_one"] = dict(
+                    seconds=tr, statuses=dict(sr), iters=[r["iters"] for r in ref], E=[r["E"] for r in ref],
+                    both_converged=len(both), same_energy=sum(abs(d) <= 1e-9 for d in dE),
+                    lower_energy_batched=sum(d < -1e-9 for d in dE), higher_energy_batched=sum(d > 1e-9 for d in dE),
+                    speedup=tr / t)
+                log(f"reference, one by one in binary64: {tr:.1f} s, {dict(sr)}; batched/reference energies: "
+                    f"{out['reference_f64_one_by_one']['same_energy']} same, "
+                    f"{out['reference_f64_one_by_one']['lower_energy_batched']} lower, "
+                    f"{out['reference_f64_one_by_one']['higher_energy_batched']} higher of {len(both)}")
     finally:
         for pl in plans:
             pl.close()
@@ -73,15 +93,16 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=48)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--full-iters", type=int, default=3000, help="0 skips the run to the tolerance")
+    ap.add_argument("--reference", action="store_true", help="also solve each instance alone in binary64")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     B.load_library()
-    res = run(W.sweep_instances(a.count), W.initial_guess, a.iters, a.full_iters)
+    res = run(W.sweep_instances(a.count), W.initial_guess, a.iters, a.full_iters, reference=a.reference)
     js = json.dumps(res)
     if a.out:
         with open(a.out, "w") as fh:
             fh.write(js + "\n")
-    print(json.dumps({k: v for k, v in res.items() if k not in ("grids", "full")}))
+    print(json.dumps({k: v for k, v in res.items() if k not in ("grids", "full", "reference_f64_one_by_one")}))
 
 
 if __name__ == "__main__":
