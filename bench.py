@@ -62,12 +62,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true", help="skip the FP32-bulk arm")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solves to 1e-8")
-    ap.add_argument("--ttt", default="f64,f32_f64,df32_split",
-                    help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split)")
+    ap.add_argument("--ttt", default="f64,f32_f64,df32_split,df32_split_all",
+                    help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split; "
+                         "a form runs on the finest level, or on every level with the suffix _all)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
                                                "profiling_overhead", "polish_df32", "fp64_peak", "iterations",
-                                               "virial_vs_tol", "engines"],
+                                               "virial_vs_tol", "engines", "finest_level", "basin",
+                                               "f32_floor", "mg_policy"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture, or one of the "
                          "timings quoted in the design notes, and exit")
     a = ap.parse_args()
@@ -366,6 +368,17 @@ TTT_FORMS = {
 }
 
 
+def parse_form(name):
+    """'<form>[_auto][_all]' -> (form, automatic hand-over, every level)."""
+    every = name.endswith("_all")
+    base = name[:-4] if every else name
+    auto = base.endswith("_auto")
+    base = base[:-5] if auto else base
+    if base not in TTT_FORMS:
+        raise ValueError(f"unknown precision form {name!r}")
+    return base, auto, every
+
+
 def time_to_tol(B, w, forms):
     """Time to residual 1e-8 through the public API, end to end: psi_0 (guess
     (d) on the coarsest grid) copied from pinned host memory, PCG-ATKM-MG
@@ -373,7 +386,12 @@ def time_to_tol(B, w, forms):
     final state copied back; wall time around all of it.  One solve per
     precision form, each compared with the binary64 solve (relative E and mu
     differences, and Phi of the final state in FP32 and double-word against
-    binary64)."""
+    binary64).  A precision form runs on the finest level, the coarser
+    levels in binary64 (mg_f64_levels = 2: the vortex configuration is
+    chosen on the coarse levels, where FP32 rounding can change it); with
+    the suffix "_all" it runs on every level; with "_auto" its FP32 phase
+    hands over at the FP32 noise of the residual measured at the start
+    (switch_tol < 0) instead of at residual 1e-5."""
     import torch
     import atkm_workloads as W
     from paper_2603_05194_gb300 import multigrid as MG
@@ -384,7 +402,9 @@ def time_to_tol(B, w, forms):
            "grids": [list(g) for g in grids], "forms": {}}
     finals = {}
     for name in forms:
-        prec = getattr(B, TTT_FORMS[name][0])
+        base, auto, every = parse_form(name)
+        prec = getattr(B, TTT_FORMS[base][0])
+        f64_levels = 0 if every or prec == B.PRECISION_F64 else len(grids) - 1
         f32 = prec != B.PRECISION_F64
         plans = [B.Plan(N, w.L, w.n, f32=f32, df32=prec == B.PRECISION_DF32_SPLIT) for N in grids]
         try:
@@ -394,7 +414,8 @@ def time_to_tol(B, w, forms):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             psis[0].copy_(psi0_host, non_blocking=True)
-            res = B.pcg_ground_state_mg(plans, prm, psis, tol_residual=TOL, max_iter=20000, precision=prec)
+            res = B.pcg_ground_state_mg(plans, prm, psis, tol_residual=TOL, max_iter=20000, precision=prec,
+                                        mg_f64_levels=f64_levels, switch_tol=-1e-5 if auto else 1e-5)
             host_out.copy_(psis[-1], non_blocking=True)
             torch.cuda.synchronize()
             sec = time.perf_counter() - t0
@@ -405,7 +426,8 @@ def time_to_tol(B, w, forms):
         out["forms"][name] = {"seconds": round(sec, 3), "status": res[-1]["status_name"], "E": res[-1]["E"],
                               "mu": res[-1]["mu"], "residual": res[-1]["residual"],
                               "iters": [r["iters"] for r in res], "f32_iters": [r["f32_iters"] for r in res],
-                              "arithmetic": TTT_FORMS[name][1]}
+                              "arithmetic": TTT_FORMS[base][1], "levels_in_binary64": f64_levels,
+                              "switch_residual": [r["switch_residual"] for r in res]}
     if "f64" in out["forms"]:
         ref = out["forms"]["f64"]
         for name, d in out["forms"].items():
@@ -694,6 +716,157 @@ def engines_case():
         print(json.dumps(row), flush=True)
 
 
+def forms_case(case: str):
+    """finest_level: where the iterations of a multigrid solve go, form by
+    form, from one common start: binary64 PCG-ATKM-MG on the two coarser
+    levels (guess (d)), the state spectrally interpolated to the finest grid,
+    then Algorithm 1 to residual 1e-8 there in each precision form from that
+    same state, with the per-iteration log (iterations to residual 1e-5, 1e-6,
+    1e-7, the FP32 iterations and the residual at the hand-over), on the bench
+    workload and on Example 3.1 Case II at 256^3.
+    basin: the bench workload's binary64 multigrid solve from guess (d)
+    twice (the solve is deterministic) and once from guess (d) with a seeded
+    relative perturbation of 1e-12: the vortex lattice it ends in, and so the
+    final energy, depends on rounding-level differences of the trajectory."""
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+    from paper_2603_05194_gb300 import multigrid as MG
+
+    def mg(w, psi0, levels):
+        plans = [B.Plan(N, w.L, w.n) for N in levels]
+        try:
+            psis = [torch.empty(p.shape, dtype=torch.complex128, device="cuda") for p in plans]
+            psis[0].copy_(torch.from_numpy(psi0))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = B.pcg_ground_state_mg(plans, B.make_params(w.gamma, w.beta, w.lam, w.Omega), psis,
+                                        tol_residual=TOL, max_iter=20000)
+            torch.cuda.synchronize()
+            return res, psis, plans, time.perf_counter() - t0
+        except Exception:
+            for p in plans:
+                p.close()
+            raise
+
+    def common_start(w):
+        grids = MG.level_grids(w.N, 3)
+        res, psis, plans, sec = mg(w, W.initial_guess(W.with_grid(w, grids[0])), grids[:2])
+        fine = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
+        start = B.spectral_upsample(plans[1], fine, psis[1])
+        torch.cuda.synchronize()
+        for p in plans:
+            p.close()
+        return fine, start
+
+    if case == "f32_floor":
+        # residual traces from the common start: the FP32 phase never handing
+        # over (switch_tol 1e-12, no stagnation window), and binary64
+        for name, cap in ((WORKLOAD, 1500), ("ex31_caseII_256", 300)):
+            w = W.CONFIGS[name] if name in W.CONFIGS else W.PAPER_WORKLOADS[name]
+            fine, start = common_start(w)
+            try:
+                prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
+                for form, kw in (("f32_f64", dict(switch_tol=1e-12, f32_window=10 ** 8)), ("f64", {})):
+                    psi = start.clone()
+                    r = fine.pcg_ground_state(prm, psi, tol_residual=TOL, max_iter=cap,
+                                              precision=getattr(B, TTT_FORMS[form][0]), log_capacity=cap + 2, **kw)
+                    trace = [float(f"{e['residual']:.4g}") for e in r["log"] if form == "f64" or e["f32_phase"]]
+                    print(json.dumps({"case": case, "workload": w.name, "form": form, "iters": r["iters"],
+                                      "f32_iters": r["f32_iters"], "residual_trace": trace}), flush=True)
+            finally:
+                fine.close()
+        return
+    if case == "mg_policy":
+        # multigrid to 1e-8 on the bench workload in binary64 and in the
+        # precision forms with the coarsest levels in binary64 and/or the
+        # FP32 phase's progress factor 0.9
+        w = W.CONFIGS[WORKLOAD]
+        grids = MG.level_grids(w.N, 3)
+        psi0 = torch.from_numpy(W.initial_guess(W.with_grid(w, grids[0])))
+        E64 = None
+        for form, kw in (("f64", {}), ("df32_split", dict(mg_f64_levels=1)), ("df32_split", dict(mg_f64_levels=2)),
+                         ("df32_split", dict(f32_gain=0.9)), ("df32_split", dict(mg_f64_levels=1, f32_gain=0.9)),
+                         ("f32_f64", dict(mg_f64_levels=1)), ("f32_f64", dict(mg_f64_levels=1, f32_gain=0.9))):
+            prec = getattr(B, TTT_FORMS[form][0])
+            plans = [B.Plan(N, w.L, w.n, f32=prec != B.PRECISION_F64, df32=prec == B.PRECISION_DF32_SPLIT)
+                     for N in grids]
+            try:
+                psis = [torch.empty(pl.shape, dtype=torch.complex128, device="cuda") for pl in plans]
+                psis[0].copy_(psi0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = B.pcg_ground_state_mg(plans, B.make_params(w.gamma, w.beta, w.lam, w.Omega), psis,
+                                            tol_residual=TOL, max_iter=20000, precision=prec, **kw)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t0
+            finally:
+                for pl in plans:
+                    pl.close()
+            E = res[-1]["E"]
+            E64 = E if form == "f64" else E64
+            print(json.dumps({"case": case, "workload": w.name, "form": form, **kw, "seconds": round(sec, 3),
+                              "status": res[-1]["status_name"], "iters": [r["iters"] for r in res],
+                              "f32_iters": [r["f32_iters"] for r in res], "E": E,
+                              "E_rel_vs_f64": abs(E - E64) / abs(E64)}), flush=True)
+        return
+    if case == "basin":
+        w = W.CONFIGS[WORKLOAD]
+        grids = MG.level_grids(w.N, 3)
+        g0 = W.initial_guess(W.with_grid(w, grids[0]))
+        xi = W.random_field(g0.shape, 77)
+        for label, psi0 in (("guess_d", g0), ("guess_d_again", g0), ("guess_d_perturbed_1e-12", g0 * (1 + 1e-12 * xi))):
+            res, _, plans, sec = mg(w, psi0, grids)
+            for p in plans:
+                p.close()
+            print(json.dumps({"case": case, "workload": w.name, "start": label, "seconds": round(sec, 3),
+                              "status": res[-1]["status_name"], "iters": [r["iters"] for r in res],
+                              "E": res[-1]["E"], "mu": res[-1]["mu"]}), flush=True)
+        return
+    for name in (WORKLOAD, "ex31_caseII_256"):
+        w = W.CONFIGS[name] if name in W.CONFIGS else W.PAPER_WORKLOADS[name]
+        grids = MG.level_grids(w.N, 3)
+        res, psis, plans, sec = mg(w, W.initial_guess(W.with_grid(w, grids[0])), grids[:2])
+        fine = B.Plan(w.N, w.L, w.n, f32=True, df32=True)
+        try:
+            start = B.spectral_upsample(plans[1], fine, psis[1])
+            prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
+            rows = {}
+            for form in ("f64", "f32_f64", "df32_split", "f32_f64_auto", "df32_split_auto"):
+                base, auto, _ = parse_form(form)
+                psi = start.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = fine.pcg_ground_state(prm, psi, tol_residual=TOL, max_iter=20000,
+                                          precision=getattr(B, TTT_FORMS[base][0]), log_capacity=20002,
+                                          switch_tol=-1e-5 if auto else 1e-5)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t0
+                log = r["log"]
+
+                def first(th):
+                    return next((e["n"] for e in log if e["residual"] <= th), None)
+                f32 = [e for e in log if e["f32_phase"]]
+                row = {"case": case, "workload": w.name, "grid": list(w.N), "form": form, "seconds": round(sec, 3),
+                       "status": r["status_name"], "iters": r["iters"], "f32_iters": r["f32_iters"],
+                       "halvings": r["halvings"], "E": r["E"], "mu": r["mu"], "switch_residual": r["switch_residual"],
+                       "start_residual": log[0]["residual"] if log else None,
+                       "iter_to_1e-5": first(1e-5), "iter_to_1e-6": first(1e-6), "iter_to_1e-7": first(1e-7),
+                       "handover_residual": f32[-1]["residual"] if f32 else None,
+                       "best_f32_residual": min(e["residual"] for e in f32) if f32 else None}
+                rows[form] = row
+            for form, row in rows.items():
+                ref = rows["f64"]
+                row["E_rel_vs_f64"] = abs(row["E"] - ref["E"]) / abs(ref["E"])
+                row["mu_rel_vs_f64"] = abs(row["mu"] - ref["mu"]) / abs(ref["mu"])
+                row["speedup_vs_f64"] = round(ref["seconds"] / row["seconds"], 3)
+                print(json.dumps(row), flush=True)
+        finally:
+            fine.close()
+            for p in plans:
+                p.close()
+
+
 def profile_case(case: str):
     """Small fixed workloads on the bench grid for ncu captures (about 1 GB of
     device memory): two ATKM evaluations, or three PCG iterations; or a
@@ -707,6 +880,9 @@ def profile_case(case: str):
         return
     if case == "engines":
         engines_case()
+        return
+    if case in ("finest_level", "basin", "f32_floor", "mg_policy"):
+        forms_case(case)
         return
     if case == "fp64_peak":
         from paper_2603_05194_gb300 import binding as B
@@ -728,7 +904,8 @@ def profile_case(case: str):
     else:
         prm = B.make_params(w.gamma, w.beta, w.lam, w.Omega)
         prec = B.PRECISION_F64 if case == "pcg_f64" else B.PRECISION_F32_F64
-        r = plan.pcg_ground_state(prm, psi, max_iter=3, precision=prec)
+        # direct launches (ncu does not profile kernel nodes of graphs with conditional nodes)
+        r = plan.pcg_ground_state(prm, psi, max_iter=3, precision=prec, graphs=False)
         torch.cuda.synchronize()
         print(case, r["status_name"], r["iters"], r["E"])
 
@@ -781,10 +958,23 @@ def main():
                    "single_thread": {"atkm_evals_per_s": round(s["value_1thread_atkm"], 4), "cores": 1,
                                      "sample": f"one stand-alone ATKM evaluation, one thread "
                                                f"({s['atkm_1thread_s']:.2f} s)"},
-                   "allcores_standalone_atkm_s": round(s["atkm_allcores_s"], 3)}
+                   "allcores_standalone_atkm_s": round(s["atkm_allcores_s"], 3),
+                   "iteration_s": round(s["iter_s"], 3)}
         except Exception as exc:  # reported, not fatal
             cpu = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                    "sample": f"failed: {exc}"[:300]}
+    if rank == 0 and cpu is not None and cpu.get("value") and out["ttt"] is not None:
+        # the oracle's time to 1e-8, extrapolated: its measured time per
+        # iteration at the finest grid times the binary64 GPU solve's
+        # iteration counts per level, the coarser levels scaled by their
+        # point counts (1/64 and 1/8)
+        it = out["ttt"]["forms"].get("f64", {}).get("iters")
+        if it and len(it) == 3:
+            per = cpu["iteration_s"]
+            est = per * (it[2] + it[1] / 8.0 + it[0] / 64.0)
+            cpu["time_to_1e-8_extrapolated_s"] = round(est, 1)
+            cpu["time_to_1e-8_note"] = (f"extrapolation, not a run: {per:.2f} s per iteration x the binary64 "
+                                        f"multigrid iteration counts {it} (coarser levels scaled by 1/64, 1/8)")
     if rank == 0:
         res = out["res"]
         value = out["evals"] / (out["ms"] * 1e-3)

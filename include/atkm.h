@@ -57,15 +57,17 @@ typedef struct atkm_plan atkm_plan;
                                      register engine covers them (3 * 2^a and 5 * 2^a,
                                      20 <= L <= 384); for comparisons, same results to
                                      rounding                                            */
+#define ATKM_PLAN_AUTOTUNE 8u     /* run atkm_plan_autotune at creation                   */
 
 /*
  * atkm_plan_create -- grid, box, dipole axis; precomputes the truncated-kernel
- * multiplier ("Precompute the coefficients", Algorithm 1; §2.2 remark: once
- * per domain and mesh).
+ * multiplier (the set-up step of Algorithm 1; §2.2 remark: once per domain
+ * and mesh).
  *   N[3]  grid sizes (N_x, N_y, N_z), see conventions.
  *   L[3]  box half-lengths, each > 0 and finite.
  *   n[3]  dipole orientation; | |n| - 1 | must be <= 1e-12 (Eq. (DDI-3D)).
- *   flags ATKM_PLAN_F64, or any of ATKM_PLAN_F32 and ATKM_PLAN_DF32.
+ *   flags ATKM_PLAN_F64, or any of ATKM_PLAN_F32, ATKM_PLAN_DF32,
+ *         ATKM_PLAN_GENERIC_FFT and ATKM_PLAN_AUTOTUNE.
  * Builds, in FP64 on the device, U0(nu) = int_{D_2L} e^{-i nu.y}/(4 pi|y|) dy on
  * the nonnegative frequency octant of the twofold-padded grid (Eq. (FUk)),
  * and from it the dipolar multiplier K = -1 + 3 (n.nu)^2 U0, symmetrised on the
@@ -122,6 +124,39 @@ unsigned long long atkm_launch_count(void);
  * Measurement support; the paper has no counterpart.
  */
 int atkm_measure_fp64_fma(int blocks_per_sm, int iters, int repeats, double* gflops, void* stream);
+
+/*
+ * atkm_plan_autotune -- FFT-tile autotuner: for every line length of the
+ * plan's passes that is not a power of two, per arithmetic the plan carries
+ * (binary64; FP32 with ATKM_PLAN_F32; double-word with ATKM_PLAN_DF32) and per
+ * layout (line-major x pass, strided y / z pass), times the candidates -- the
+ * mixed-radix register engine (lengths 3 * 2^a, 5 * 2^a <= 384; not double-
+ * word; not with ATKM_PLAN_GENERIC_FFT) and the generic shared-memory engine
+ * at its default tile width, 1/2 and 1/4 of it -- on the plan's own ATKM of
+ * |psi|^2, H psi and P r (CUDA events on `stream`, best of 3 after a warm-up)
+ * and keeps the fastest; every later pass of that length and layout uses it.
+ * Power-of-two lengths keep the power-of-two register engine.  Results change
+ * only by rounding.  Allocates and frees scratch of about 40 bytes a grid
+ * point; synchronises `stream`.  Must run before the plan's first PCG solve
+ * (ATKM_ERR_ARG afterwards).  Selection support; the paper has no
+ * counterpart.
+ */
+int atkm_plan_autotune(atkm_plan* plan, void* stream);
+
+typedef struct atkm_tune_info {
+  int precision;   /* 0 binary64, 1 FP32, 2 double-word                        */
+  int length;      /* line length L                                            */
+  int line_major;  /* 1: the x pass (contiguous lines), 0: a strided y / z pass */
+  int engine;      /* 1: mixed-radix register engine, 2: generic engine        */
+  int tile_shift;  /* generic engine: tile width = default >> tile_shift       */
+  int pad_;
+  double ms_default;  /* the timed operators under the fixed rule, ms          */
+  double ms_best;     /* under the chosen candidate, ms                        */
+} atkm_tune_info;
+
+/* Copies up to `cap` of the plan's autotuned choices to out (host); returns
+ * how many the plan holds (0 when not tuned), or -ATKM_ERR_ARG. */
+int atkm_plan_tuning(const atkm_plan* plan, atkm_tune_info* out, int cap);
 
 /* on != 0 clears the record and starts recording; on == 0 stops. */
 int atkm_plan_set_profiling(atkm_plan* plan, int on);
@@ -223,7 +258,8 @@ int apply_preconditioner(atkm_plan* plan, const atkm_params* prm, double alpha, 
 #define ATKM_PRECISION_F64 0      /* every step in FP64                          */
 #define ATKM_PRECISION_F32_F64 1  /* complex64 FFT/ATKM/H/P until switch_tol, two exhausted
                                      halving loops, or f32_window iterations without
-                                     halving the best FP32 residual; then FP64          */
+                                     the best FP32 residual falling by the factor
+                                     f32_gain; then FP64                                */
 #define ATKM_PRECISION_F32_SPLIT 2 /* as ATKM_PRECISION_F32_F64, and after the hand-over the
                                      operators that only shape the search direction and
                                      the step-size model (P r, H p and the ATKM of
@@ -244,7 +280,12 @@ typedef struct atkm_pcg_opts {
   int max_iter;         /* iteration cap (ATKM_NOT_CONVERGED when reached)            */
   int max_halvings;     /* halvings of t per iteration before taking the lowest trial */
   int precision_mode;   /* ATKM_PRECISION_F64 or ATKM_PRECISION_F32_F64               */
-  double switch_tol;    /* residual at which the F32 phase hands over (e.g. 1e-5)     */
+  double switch_tol;    /* residual at which the F32 phase hands over (e.g. 1e-5); if
+                           < 0, automatic: the larger of |switch_tol| and 4x the
+                           FP32 noise of the residual, measured once at phi_0 as
+                           ||H phi_0 in FP32 - H phi_0 in FP64|| (each with its
+                           own ATKM; about one FP64 iteration of extra work), and
+                           the stagnation window's default becomes 2000         */
   int log_capacity;     /* entries available in `log` (0 = no log)                    */
   int resume;           /* != 0: continue the solve this plan ran last (psi_inout is
                            then output only); the iteration count, direction memory,
@@ -259,6 +300,13 @@ typedef struct atkm_pcg_opts {
                            state reached is returned and can be resumed          */
   int f32_window;       /* precision forms: FP32-phase iterations without halving the
                            best FP32 residual before the hand-over (0: 50)       */
+  double f32_gain;      /* precision forms: the factor by which the best FP32
+                           residual must fall within f32_window iterations for
+                           the FP32 phase to go on (0: 0.5, "halving"; 0.9 lets
+                           slow but steady progress continue)                   */
+  int mg_f64_levels;    /* pcg_ground_state_mg with a precision form: the number of
+                           coarsest levels solved in FP64 (0: none); ignored by the
+                           single-level calls                                   */
 } atkm_pcg_opts;
 
 /* One record per iteration n (values at phi_n; step fields describe n -> n+1). */
@@ -275,6 +323,8 @@ typedef struct atkm_result {
   int log_count;        /* entries written                                       */
   int device_loop;      /* 1 when the device-driven graph ran the iterations, 0 when
                            the host took the decisions between them              */
+  double switch_residual; /* precision forms: the residual at which the FP32 phase
+                           hands over (see atkm_pcg_opts.switch_tol); 0 in FP64  */
 } atkm_result;
 
 /*
@@ -335,7 +385,8 @@ int atkm_spectral_upsample(atkm_plan* coarse, atkm_plan* fine, const double* psi
 /*
  * pcg_ground_state_mg -- the cascadic multigrid driver PCG-ATKM-MG
  * (Algorithm 2): for level i = 0 .. levels-1 (coarse to fine), compute the
- * ground state on plans[i] by Algorithm 1 (pcg_ground_state with `opts`)
+ * ground state on plans[i] by Algorithm 1 (pcg_ground_state with `opts`;
+ * with a precision form, the opts.mg_f64_levels coarsest levels in FP64)
  * starting from psi[i], then (Step 2) set psi[i+1] to its Fourier interpolant
  * on the next grid (atkm_spectral_upsample).  The plans share the box and the
  * dipole axis; grids must not get coarser.  The paper's setting is three

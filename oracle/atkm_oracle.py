@@ -223,8 +223,8 @@ def truncated_convolution(rho, mult):
 
 
 class Plan:
-    """Grid, box, dipole axis and the precomputed multiplier (Algorithm 1,
-    'Precompute the coefficients')."""
+    """Grid, box, dipole axis and the precomputed multiplier (the set-up
+    step of Algorithm 1; §2.2: once per domain and mesh)."""
 
     def __init__(self, N, L, n):
         nn = math.sqrt(sum(v * v for v in n))

@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED_SIZE", 3: "ERR_OOM", 
 ATKM_PLAN_F32 = 1
 ATKM_PLAN_DF32 = 2
 ATKM_PLAN_GENERIC_FFT = 4
+ATKM_PLAN_AUTOTUNE = 8
 PRECISION_F64 = 0
 PRECISION_F32_F64 = 1
 PRECISION_F32_SPLIT = 2
@@ -52,7 +53,7 @@ class PcgOpts(C.Structure):
     _fields_ = [("tol_residual", C.c_double), ("tol_linf", C.c_double), ("max_iter", C.c_int),
                 ("max_halvings", C.c_int), ("precision_mode", C.c_int), ("switch_tol", C.c_double),
                 ("log_capacity", C.c_int), ("resume", C.c_int), ("no_graphs", C.c_int), ("time_limit_s", C.c_double),
-                ("f32_window", C.c_int)]
+                ("f32_window", C.c_int), ("f32_gain", C.c_double), ("mg_f64_levels", C.c_int)]
 
 
 class IterLog(C.Structure):
@@ -60,6 +61,11 @@ class IterLog(C.Structure):
                 ("f32_phase", C.c_int), ("pad_", C.c_int)] + \
                [(k, C.c_double) for k in ("E", "mu", "residual", "linf_step", "alpha", "beta_cg", "d1",
                                           "curvature", "t0", "t")]
+
+
+class TuneInfo(C.Structure):
+    _fields_ = [("precision", C.c_int), ("length", C.c_int), ("line_major", C.c_int), ("engine", C.c_int),
+                ("tile_shift", C.c_int), ("pad_", C.c_int), ("ms_default", C.c_double), ("ms_best", C.c_double)]
 
 
 class KernelStat(C.Structure):
@@ -71,7 +77,8 @@ class Result(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("E", "mu", "E_kin", "E_pot", "E_int", "E_dip", "E_rot", "virial",
                                           "residual", "linf_step")] + \
                [("iters", C.c_int), ("halvings", C.c_int), ("f32_iters", C.c_int), ("status", C.c_int),
-                ("log", C.POINTER(IterLog)), ("log_count", C.c_int), ("device_loop", C.c_int)]
+                ("log", C.POINTER(IterLog)), ("log_count", C.c_int), ("device_loop", C.c_int),
+                ("switch_residual", C.c_double)]
 
 
 _lib = None
@@ -123,6 +130,8 @@ def load_library(path: str = LIB_PATH):
         "atkm_inner_products_noalloc": (ip, [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_ulonglong, C.c_double, vp,
                                              vp]),
         "atkm_plan_kernel_stats": (ip, [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]),
+        "atkm_plan_autotune": (ip, [vp, vp]),
+        "atkm_plan_tuning": (ip, [vp, C.POINTER(TuneInfo), C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -134,7 +143,7 @@ def load_library(path: str = LIB_PATH):
 
 def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, max_iter=10000, max_halvings=20,
                              precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True,
-                             time_limit_s=0.0, f32_window=0) -> list:
+                             time_limit_s=0.0, f32_window=0, f32_gain=0.0) -> list:
     """Runs independent solves (one plan each, grids may differ) concurrently
     through pcg_ground_state_batched; returns one result dict per instance."""
     lib = load_library()
@@ -144,7 +153,7 @@ def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.
     for pl, ps in zip(plans, psis):
         _ptr(ps, torch.complex128, pl.shape, "psi")
     opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1,
-                   time_limit_s, f32_window)
+                   time_limit_s, f32_window, f32_gain, 0)
     ph = (C.c_void_p * n)(*[pl._h for pl in plans])
     pa = (Params * n)(*params)
     pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
@@ -162,9 +171,10 @@ def pcg_ground_state_batched(plans, params, psis, tol_residual=1e-8, tol_linf=0.
 
 def pcg_ground_state_mg(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, max_iter=10000, max_halvings=20,
                         precision=PRECISION_F64, switch_tol=1e-5, stream=None, graphs=True, time_limit_s=0.0,
-                        f32_window=0) -> list:
+                        f32_window=0, f32_gain=0.0, mg_f64_levels=0) -> list:
     """Cascadic multigrid PCG-ATKM-MG through pcg_ground_state_mg: plans and
-    psis from the coarsest level to the finest, psis[0] the initial guess.
+    psis from the coarsest level to the finest, psis[0] the initial guess;
+    with a precision form the mg_f64_levels coarsest levels run in FP64.
     Returns one result dict per level."""
     lib = load_library()
     n = len(plans)
@@ -173,7 +183,7 @@ def pcg_ground_state_mg(plans, params, psis, tol_residual=1e-8, tol_linf=0.0, ma
     for pl, ps in zip(plans, psis):
         _ptr(ps, torch.complex128, pl.shape, "psi")
     opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, 0, 0, 0 if graphs else 1,
-                   time_limit_s, f32_window)
+                   time_limit_s, f32_window, f32_gain, mg_f64_levels)
     ph = (C.c_void_p * n)(*[pl._h for pl in plans])
     pp = (C.c_void_p * n)(*[C.c_void_p(t.data_ptr()) for t in psis])
     res = (Result * n)()
@@ -344,7 +354,8 @@ def make_params(gamma, beta, lam, Omega) -> Params:
 class Plan:
     """Owning handle of an atkm_plan (grid, box, dipole axis, multiplier)."""
 
-    def __init__(self, N, L, n, f32: bool = False, stream=None, df32: bool = False, generic_fft: bool = False):
+    def __init__(self, N, L, n, f32: bool = False, stream=None, df32: bool = False, generic_fft: bool = False,
+                 autotune: bool = False):
         lib = load_library()
         self.N = tuple(int(v) for v in N)
         self.L = tuple(float(v) for v in L)
@@ -355,7 +366,7 @@ class Plan:
         La = (C.c_double * 3)(*self.L)
         na = (C.c_double * 3)(*self.n)
         flags = (ATKM_PLAN_F32 if f32 else 0) | (ATKM_PLAN_DF32 if df32 else 0) | \
-            (ATKM_PLAN_GENERIC_FFT if generic_fft else 0)
+            (ATKM_PLAN_GENERIC_FFT if generic_fft else 0) | (ATKM_PLAN_AUTOTUNE if autotune else 0)
         code = lib.atkm_plan_create(C.byref(self._h), Na, La, na, flags, _stream(stream))
         if code != ATKM_OK:
             raise AtkmError(code, lib.atkm_last_error_string(None).decode())
@@ -379,6 +390,18 @@ class Plan:
     @property
     def device_bytes(self) -> int:
         return int(self._lib.atkm_plan_device_bytes(self._h))
+
+    # ---- FFT-tile autotuner
+    def autotune(self, stream=None):
+        self._check(self._lib.atkm_plan_autotune(self._h, _stream(stream)))
+
+    def tuning(self) -> list:
+        cap = 64
+        arr = (TuneInfo * cap)()
+        n = self._lib.atkm_plan_tuning(self._h, arr, cap)
+        if n < 0:
+            raise AtkmError(-n, "atkm_plan_tuning")
+        return [{k: getattr(arr[i], k) for k, _ in TuneInfo._fields_ if k != "pad_"} for i in range(min(n, cap))]
 
     # ---- measurement support
     def set_profiling(self, on: bool):
@@ -454,9 +477,9 @@ class Plan:
     def pcg_ground_state(self, prm: Params, psi, tol_residual=1e-8, tol_linf=0.0, max_iter=10000,
                          max_halvings=20, precision=PRECISION_F64, switch_tol=1e-5, log_capacity=0,
                          stream=None, check=True, resume=False, graphs=True, time_limit_s=0.0,
-                         f32_window=0) -> dict:
+                         f32_window=0, f32_gain=0.0) -> dict:
         opts = PcgOpts(tol_residual, tol_linf, max_iter, max_halvings, precision, switch_tol, log_capacity,
-                       1 if resume else 0, 0 if graphs else 1, time_limit_s, f32_window)
+                       1 if resume else 0, 0 if graphs else 1, time_limit_s, f32_window, f32_gain, 0)
         res = Result()
         logs = (IterLog * max(1, log_capacity))()
         res.log = C.cast(logs, C.POINTER(IterLog)) if log_capacity > 0 else C.POINTER(IterLog)()

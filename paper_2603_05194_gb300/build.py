@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libatkm.so")
 SOURCES = ["plan.cu", "passes_f64.cu", "passes_f64_a.cu", "passes_f64_h.cu", "passes_f32.cu", "passes_f32_a.cu",
            "passes_f32_h.cu", "passes_df.cu", "passes_df_ax.cu", "passes_df_ay.cu",
-           "passes_df_az.cu", "passes_df_h.cu", "passes_df_hx.cu", "passes_df_hy.cu", "passes_df_hz.cu", "pcg.cu", "noalloc.cu", "guess_net.cu", "measure.cu"]
+           "passes_df_az.cu", "passes_df_h.cu", "passes_df_hx.cu", "passes_df_hy.cu", "passes_df_hz.cu", "pcg.cu", "noalloc.cu", "guess_net.cu", "measure.cu",
+           "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

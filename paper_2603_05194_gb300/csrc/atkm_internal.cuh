@@ -31,22 +31,22 @@ template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
 // share the slow FP64 pipe on this part).  binary64 -> binary32 rounds the 29
 // dropped mantissa bits half-up (a mantissa carry moves into the exponent),
 // flushes results below the binary32 normal range to signed zero and
-// saturates to infinity; binary32 -> binary64 is exact for normal numbers and
-// flushes binary32 subnormals to signed zero.
+// saturates to infinity (a NaN becomes an infinity); binary32 -> binary64 is
+// exact for normal numbers and flushes binary32 subnormals to signed zero.
 __device__ __forceinline__ float d2f_bits(double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  const unsigned int hi = (unsigned int)(u >> 32);
-  const unsigned int sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e >= 255) {
-    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (u & 0x000fffffffffffffull) != 0ull;
-    return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
-  }
-  if (e <= 0) return __uint_as_float(sign);
-  const unsigned long long m = u & 0x000fffffffffffffull;
-  unsigned int bits = ((unsigned int)e << 23) + (unsigned int)((m + (1ull << 28)) >> 29);
-  if (bits >= 0x7f800000u) bits = 0x7f800000u;
-  return __uint_as_float(sign | bits);
+  const unsigned int hi = (unsigned int)__double2hiint(d), lo = (unsigned int)__double2loint(d);
+  // the high word with the exponent rebased to binary32: (e32 << 20) | the
+  // top 20 mantissa bits; e32 <= 0 flushes, e32 >= 255 saturates (a NaN
+  // becomes an infinity)
+  int a = (int)(hi & 0x7fffffffu) - 0x38000000;
+  const bool tiny = a < 0x00100000;
+  a = min(a, 0x0ff00000);
+  // (a:lo) + 2^28 rounds the 29 dropped bits half-up; bits 29..60 are the result
+  const unsigned int lr = lo + 0x10000000u;
+  const unsigned int ar = (unsigned int)a + (lr < lo ? 1u : 0u);
+  unsigned int bits = min(__funnelshift_r(lr, ar, 29), 0x7f800000u);
+  bits = tiny ? 0u : bits;
+  return __uint_as_float(bits | (hi & 0x80000000u));
 }
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned int u = __float_as_uint(f);
@@ -395,6 +395,18 @@ struct Phys {  // physical parameters passed by value to kernels
 struct PcgBuffers;  // defined in pcg.cu
 struct Profiler;    // defined in plan.cu
 
+// One choice of the FFT-tile autotuner (tune.cu): for the arithmetic r (0
+// binary64, 1 FP32, 2 double-word), the line length L and the layout lm (1:
+// line-major x pass, 0: strided pass), the engine (mix = 1: the mixed-radix
+// register engine, else the generic shared-memory engine with its default
+// tile width shifted right by `shift`), with the timed operator set's
+// milliseconds under the default rule and under this choice.
+struct TuneEntry {
+  int r, L, lm, mix, shift;
+  double ms_default, ms_best;
+};
+constexpr int kMaxTune = 48;
+
 }  // namespace atkm
 
 // Scalar slots in plan->scal (device) and their host mirror.
@@ -432,6 +444,8 @@ struct atkm_plan {
   double* scal;        // device scalars
   double* scal_host;   // pinned mirror
   atkm::PcgBuffers* pcg;
+  atkm::TuneEntry tune[atkm::kMaxTune];  // autotuned engine choices (n_tune of them)
+  int n_tune;
   atkm::Profiler* prof;  // non-null while profiling is on
   atkm::Profiler* prof_stopped_;  // last record after profiling was switched off
   unsigned long long bytes;

@@ -14,6 +14,7 @@
 // global phase are learnable): L = 1 - |<u,t>|^2 / (|u|^2 |t|^2).
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <vector>
@@ -149,13 +150,14 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 
 constexpr int kRowsThreads = 256;
 
-// C[M x N] = A[M x K] B[K x N], A rows contiguous (A(m,k) = A[m*sam + k]):
-// each thread forms NT consecutive outputs of one row; B (K x N, any
-// strides) is staged in shared memory.
+// C[M x N] = A[M x K] B[K x N] with A's rows contiguous and 16-byte aligned
+// (A(m,k) = A[m*sam + k], sam and K multiples of 4) and C's rows too (ldc a
+// multiple of 4): each thread forms NT consecutive outputs of one row from
+// float4 loads of the row; B (K x N, any strides) is staged in shared memory.
 template <int NT>
 __device__ __forceinline__ void gemm_rows(const float* __restrict__ A, long sam, const float* __restrict__ Bm, long sbk,
                                           long sbn, float* __restrict__ C, int ldc, int M, int N, int K) {
-  extern __shared__ float bsm[];  // [K][N]
+  extern __shared__ __align__(16) float bsm[];  // [K][N]
   for (int i = threadIdx.x; i < K * N; i += kRowsThreads) {
     const int k = i / N, n = i - k * N;
     bsm[i] = bf16r(Bm[(long)k * sbk + (long)n * sbn]);
@@ -169,16 +171,27 @@ __device__ __forceinline__ void gemm_rows(const float* __restrict__ A, long sam,
   float acc[NT];
 #pragma unroll
   for (int n = 0; n < NT; ++n) acc[n] = 0.f;
-  const float* a = A + row * sam;
-  for (int k = 0; k < K; ++k) {
-    const float av = bf16r(__ldg(a + k));
-    const float* b = bsm + k * N + c * NT;
+  const float4* a4 = reinterpret_cast<const float4*>(A + row * sam);
+#pragma unroll 4
+  for (int k4 = 0; k4 < K / 4; ++k4) {
+    const float4 av = __ldg(a4 + k4);
+    const float ak[4] = {bf16r(av.x), bf16r(av.y), bf16r(av.z), bf16r(av.w)};
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n] = fmaf(av, b[n], acc[n]);
+    for (int kk = 0; kk < 4; ++kk) {
+      const float4* b4 = reinterpret_cast<const float4*>(bsm + (4 * k4 + kk) * N + c * NT);
+#pragma unroll
+      for (int q = 0; q < NT / 4; ++q) {
+        const float4 bv = b4[q];
+        acc[4 * q] = fmaf(ak[kk], bv.x, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(ak[kk], bv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(ak[kk], bv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(ak[kk], bv.w, acc[4 * q + 3]);
+      }
+    }
   }
-  float* out = C + row * ldc + c * NT;
+  float4* out = reinterpret_cast<float4*>(C + row * ldc + c * NT);
 #pragma unroll
-  for (int n = 0; n < NT; ++n) out[n] = acc[n];
+  for (int q = 0; q < NT / 4; ++q) out[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 __global__ void __launch_bounds__(kRowsThreads)
 k_gemm_rows8(const float* __restrict__ A, long sam, const float* __restrict__ Bm, long sbk, long sbn,
@@ -191,60 +204,59 @@ k_gemm_rows16(const float* __restrict__ A, long sam, const float* __restrict__ B
   gemm_rows<16>(A, sam, Bm, sbk, sbn, C, ldc, M, N, K);
 }
 
-// C[M x N] += X^T Y over rows k of X (K x M, rows ldx apart) and Y (K x N,
-// rows ldy apart): each CTA stages blocks of kTnRows rows in shared memory
-// and sums its rows into per-thread outputs, then adds them into C (zeroed
-// by the caller) atomically.
-constexpr int kTnRows = 32;
+// C[M x N] += X^T Y summed over the K rows of X (K x M, rows ldx apart) and
+// Y (K x N, rows ldy apart), rows 16-byte aligned, M % 4 == 0, N % 8 == 0,
+// M N <= 8192: each thread keeps a 4 x 8 tile of C in registers (tile =
+// thread % tiles) and sums the rows of its phase (ph = thread / tiles: rows
+// k0 + ph, k0 + ph + P, ... of the CTA's range, P = 256 / tiles), from
+// float4 loads; the phases are then summed through shared memory and each
+// CTA adds its sums into C (zeroed by the caller) atomically.
+constexpr int kTnTM = 4, kTnTN = 8, kTnPad = kTnTM * kTnTN + 1;
 __global__ void __launch_bounds__(kRowsThreads)
 k_gemm_tn(const float* __restrict__ X, long ldx, const float* __restrict__ Y, long ldy, float* __restrict__ C,
           int ldc, int M, int N, long K, long rows_per_cta) {
-  extern __shared__ float tsm[];  // [kTnRows][M] then [kTnRows][N]
-  float* xs = tsm;
-  float* ys = tsm + kTnRows * M;
-  const int MN = M * N;
-  const int P = MN >= kRowsThreads ? 1 : kRowsThreads / MN;  // row phases
-  const int O = MN >= kRowsThreads ? (MN + kRowsThreads - 1) / kRowsThreads : 1;  // outputs a thread
-  const int o0 = MN >= kRowsThreads ? threadIdx.x : (int)(threadIdx.x % MN);
-  const int ph = MN >= kRowsThreads ? 0 : (int)(threadIdx.x / MN);
-  float acc[16];
+  __shared__ float red[kRowsThreads * kTnPad];
+  const int tn = N / kTnTN, tiles = (M / kTnTM) * tn;
+  const int P = kRowsThreads / tiles;
+  const int tile = threadIdx.x % tiles, ph = threadIdx.x / tiles;
+  const int m0 = (tile / tn) * kTnTM, n0 = (tile % tn) * kTnTN;
+  float acc[kTnTM][kTnTN];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  for (int i = 0; i < kTnTM; ++i)
+#pragma unroll
+    for (int j = 0; j < kTnTN; ++j) acc[i][j] = 0.f;
   const long k0 = (long)blockIdx.x * rows_per_cta, k1 = k0 + rows_per_cta < K ? k0 + rows_per_cta : K;
-  for (long kb = k0; kb < k1; kb += kTnRows) {
-    const int nr = (int)(k1 - kb < kTnRows ? k1 - kb : kTnRows);
-    for (int i = threadIdx.x; i < nr * M; i += kRowsThreads) {
-      const int r = i / M, m = i - r * M;
-      xs[i] = bf16r(X[(kb + r) * ldx + m]);
-    }
-    for (int i = threadIdx.x; i < nr * N; i += kRowsThreads) {
-      const int r = i / N, n = i - r * N;
-      ys[i] = bf16r(Y[(kb + r) * ldy + n]);
-    }
-    __syncthreads();
-    if (ph < P) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (j >= O) break;
-        const int o = o0 + j * kRowsThreads;
-        if (o >= MN) break;
-        const int m = o / N, n = o - m * N;
-        float a = acc[j];
-        for (int r = ph; r < nr; r += P) a = fmaf(xs[r * M + m], ys[r * N + n], a);
-        acc[j] = a;
-      }
-    }
-    __syncthreads();
-  }
   if (ph < P) {
+#pragma unroll 2
+    for (long r = k0 + ph; r < k1; r += P) {
+      const float4 xa = __ldg(reinterpret_cast<const float4*>(X + r * ldx + m0));
+      const float4 ya = __ldg(reinterpret_cast<const float4*>(Y + r * ldy + n0));
+      const float4 yb = __ldg(reinterpret_cast<const float4*>(Y + r * ldy + n0 + 4));
+      const float xv[kTnTM] = {bf16r(xa.x), bf16r(xa.y), bf16r(xa.z), bf16r(xa.w)};
+      const float yv[kTnTN] = {bf16r(ya.x), bf16r(ya.y), bf16r(ya.z), bf16r(ya.w),
+                               bf16r(yb.x), bf16r(yb.y), bf16r(yb.z), bf16r(yb.w)};
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (j >= O) break;
-      const int o = o0 + j * kRowsThreads;
-      if (o >= MN) break;
-      const int m = o / N, n = o - m * N;
-      atomicAdd(C + (long)m * ldc + n, acc[j]);
+      for (int i = 0; i < kTnTM; ++i)
+#pragma unroll
+        for (int j = 0; j < kTnTN; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
     }
+  }
+#pragma unroll
+  for (int i = 0; i < kTnTM; ++i)
+#pragma unroll
+    for (int j = 0; j < kTnTN; ++j) red[threadIdx.x * kTnPad + i * kTnTN + j] = acc[i][j];
+  __syncthreads();
+  // output o = (m, n): G = 256 / MN thread groups (at least 1) share its phases
+  const int MN = M * N;
+  const int G = MN >= kRowsThreads ? 1 : kRowsThreads / MN;
+  const int g = MN >= kRowsThreads ? 0 : (int)threadIdx.x / MN;
+  if (g >= G) return;
+  for (int o = MN >= kRowsThreads ? (int)threadIdx.x : (int)threadIdx.x % MN; o < MN; o += kRowsThreads) {
+    const int m = o / N, n = o - m * N;
+    const int t = (m / kTnTM) * tn + n / kTnTN, e = (m % kTnTM) * kTnTN + n % kTnTN;
+    float sum = 0.f;
+    for (int q = g; q < P; q += G) sum += red[(q * tiles + t) * kTnPad + e];
+    atomicAdd(C + (long)m * ldc + n, sum);
   }
 }
 
@@ -509,7 +521,9 @@ cudaError_t gemm(const float* A, long sam, long sak, const float* Bm, long sbk, 
 cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc,
                         int M, int N, int K, cudaStream_t st, bool split_k) {
   // row-local products: the output rows need only K x N <= 4096 weights
-  if (sak == 1 && (long)K * N <= 4096 && N % 8 == 0 && M >= 1024) {
+  const bool a16 = ((uintptr_t)A & 15) == 0 && ((uintptr_t)C & 15) == 0;
+  if (sak == 1 && (long)K * N <= 4096 && N % 8 == 0 && M >= 1024 && K % 4 == 0 && sam % 4 == 0 && ldc % 4 == 0 &&
+      a16) {
     const int nt = N % 16 == 0 ? 16 : 8;
     const long threads = (long)M * (N / nt);
     const int blocks = (int)((threads + kRowsThreads - 1) / kRowsThreads);
@@ -522,15 +536,17 @@ cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, lon
     return cudaGetLastError();
   }
   // weight gradients: M x N <= 4096 outputs summed over many rows
-  if (split_k && sam == 1 && sbn == 1 && (long)M * N <= 4096 && K >= 1024) {
+  const bool b16 = ((uintptr_t)A & 15) == 0 && ((uintptr_t)Bm & 15) == 0 && sak % 4 == 0 && sbk % 4 == 0;
+  if (split_k && sam == 1 && sbn == 1 && (long)M * N <= 4096 && K >= 1024 && M % kTnTM == 0 && N % kTnTN == 0 &&
+      b16) {
     cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * ldc * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const int nsm = std::max(device_sm_count(), 1);
-    long ctas = std::min<long>((long)nsm * 4, ((long)K + kTnRows - 1) / kTnRows);
+    const long P = kRowsThreads / ((M / kTnTM) * (N / kTnTN));
+    long ctas = std::min<long>((long)nsm * 2, std::max<long>(1, (long)K / (P * 16)));
     const long rows = ((long)K + ctas - 1) / ctas;
     ctas = ((long)K + rows - 1) / rows;
-    const size_t sm = (size_t)kTnRows * (M + N) * sizeof(float);
-    k_gemm_tn<<<(int)ctas, kRowsThreads, sm, st>>>(A, sak, Bm, sbk, C, ldc, M, N, (long)K, rows);
+    k_gemm_tn<<<(int)ctas, kRowsThreads, 0, st>>>(A, sak, Bm, sbk, C, ldc, M, N, (long)K, rows);
     count_launches(1);
     return cudaGetLastError();
   }

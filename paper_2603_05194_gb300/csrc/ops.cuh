@@ -282,6 +282,9 @@ template <int S1, bool SECOND, int NRED, bool LM> struct OpBase {
   static constexpr bool kHalfOut = false;    // only positions < L/2 of the last transform's output are used
   static constexpr bool kNyqTail = false;    // column pass over columns 0..c.Nx (see k_fast)
   static constexpr int kPre = 0;  // bytes per element the op prefetches into shared memory (fast engine)
+  // the fast engine keeps the loaded line in registers and hands each element
+  // to the epilogue (store_k / store_pre_k), which then need not load it again
+  static constexpr bool kKeepIn = false;
   double* part = nullptr;                  // reduction partials [slot][block]
   int pstride = 0;
 };
@@ -301,8 +304,15 @@ __device__ __forceinline__ void reduce_out(R (&acc)[NR], double* part, int pstri
   }
 }
 
+// CTAs per SM the fast engine is compiled for: 4 in FP32 (64 registers), 3
+// when the prefetch buffer of 16 bytes an element already limits the shared
+// memory to 3 CTAs (80 registers), 2 otherwise (128 registers).
+template <typename R, class Op> constexpr int fast_min_blocks() {
+  return sizeof(R) == 4 ? (Op::kPre >= 16 ? 3 : 4) : 2;
+}
+
 template <typename R, int L, class Op>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_fast(Op op, const cx<R>* __restrict__ twg) {
+__global__ void __launch_bounds__(kThreads, fast_min_blocks<R, Op>()) k_fast(Op op, const cx<R>* __restrict__ twg) {
   using C = FastCfg<L>;
   extern __shared__ __align__(16) unsigned char fast_smem[];
   cx<R>* tw = reinterpret_cast<cx<R>*>(fast_smem);
@@ -343,6 +353,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_fast(Op op
   cx<R> v[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) v[r] = (ok && (!Op::kZeroUpper || r < 4)) ? op.load(o, x, j + C::TPL * r) : czero<R>();
+  cx<R> vin[Op::kKeepIn ? 8 : 1];
+  if constexpr (Op::kKeepIn) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) vin[r] = v[r];
+  }
   // FP64 twiddles are staged in shared memory; FP32 twiddles are read through
   // L1 from global memory, which avoids the bank conflicts of the strided
   // table accesses (the FP32 passes are issue-bound, the FP64 ones ALU-bound).
@@ -384,12 +399,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_fast(Op op
       cp_async_wait_all();
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r)
-          op.store_pre(o, x, j + C::TPL * r, v[r], acc, pre + ((size_t)r * kThreads + threadIdx.x) * Op::kPre);
+        for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r) {
+          unsigned char* src = pre + ((size_t)r * kThreads + threadIdx.x) * Op::kPre;
+          if constexpr (Op::kKeepIn) op.store_pre_k(o, x, j + C::TPL * r, v[r], acc, src, vin[r]);
+          else op.store_pre(o, x, j + C::TPL * r, v[r], acc, src);
+        }
       }
     } else if (ok) {
 #pragma unroll
-      for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r) op.store(o, x, j + C::TPL * r, v[r], acc);
+      for (int r = 0; r < (Op::kHalfOut ? 4 : 8); ++r) {
+        if constexpr (Op::kKeepIn) op.store_k(o, x, j + C::TPL * r, v[r], acc, vin[r]);
+        else op.store(o, x, j + C::TPL * r, v[r], acc);
+      }
     }
   }
   if (Op::kRed > 0) reduce_out<R, NR>(acc, op.part, op.pstride);
@@ -484,14 +505,31 @@ bool mix_len(int L);
 // 20 complex doubles a thread make it slower than the generic engine,
 // measured), not with ATKM_PLAN_GENERIC_FFT, else the generic shared-memory
 // engine.
+template <typename R> constexpr int tune_r() {
+  return std::is_same<R, double>::value ? 0 : (std::is_same<R, float>::value ? 1 : 2);
+}
+// An autotuned choice for (R, L, LM) of this plan, or null.
+template <typename R> inline const TuneEntry* tuned(const atkm_plan* p, int L, bool LM) {
+  for (int i = 0; i < p->n_tune; ++i) {
+    const TuneEntry& e = p->tune[i];
+    if (e.r == tune_r<R>() && e.L == L && e.lm == (LM ? 1 : 0)) return &e;
+  }
+  return nullptr;
+}
+
 template <typename R> inline PassGrid pass_grid(const atkm_plan* p, int L, bool LM, long lines, int X, int outer) {
   PassGrid pg;
   pg.fast = fast_len(L);
   pg.mix = !pg.fast && !std::is_same<R, df>::value && !(p->flags & ATKM_PLAN_GENERIC_FFT) && mix_len(L) &&
            !(std::is_same<R, double>::value && L % 5 == 0);
+  const TuneEntry* te = pg.fast ? nullptr : tuned<R>(p, L, LM);
+  if (te) pg.mix = te->mix != 0 && mix_len(L) && !std::is_same<R, df>::value;
   if (pg.fast) pg.T = kFastElems / L;
   else if (pg.mix) pg.T = kThreads / (L / (L % 3 == 0 ? 12 : 20));
-  else pg.T = LM ? gen_lm_tile<R>(L, lines) : gen_col_tile<R>(L, X, outer);
+  else {
+    pg.T = LM ? gen_lm_tile<R>(L, lines) : gen_col_tile<R>(L, X, outer);
+    if (te) pg.T = std::max(pg.T >> te->shift, 1);
+  }
   if (LM) pg.grid = dim3(ceil_div_l(lines, pg.T), 1, 1);
   else pg.grid = dim3(ceil_div_l(X, pg.T), outer, 1);
   return pg;
@@ -809,7 +847,14 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R* a) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
-    finish(o, x, pos, idx, v, a, tor<R>(ldro(Phi + idx)), ldro(acc + idx));
+    finish(o, x, pos, idx, v, a, tor<R>(ldro(Phi + idx)), ldro(acc + idx), from64<R>(ldro(f + idx)));
+  }
+  // FP32 and double-word: f at this point is the element the engine loaded
+  // (the same conversion of the same value), kept in registers
+  static constexpr bool kKeepIn = !std::is_same<R, double>::value;
+  __device__ void store_k(int o, int x, int pos, cx<R> v, R* a, cx<R> fin) const {
+    const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
+    finish(o, x, pos, idx, v, a, tor<R>(ldro(Phi + idx)), ldro(acc + idx), fin);
   }
   // FP32: Phi (8 B) and the accumulator (8 B) are prefetched into shared memory
   static constexpr int kPre = std::is_same<R, float>::value ? 16 : 0;
@@ -821,9 +866,15 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   __device__ void store_pre(int o, int x, int pos, cx<R> v, R* a, const unsigned char* src) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
     finish(o, x, pos, idx, v, a, tor<R>(*reinterpret_cast<const double*>(src)),
-           *reinterpret_cast<const cx<R>*>(src + 8));
+           *reinterpret_cast<const cx<R>*>(src + 8), from64<R>(ldro(f + idx)));
   }
-  __device__ __forceinline__ void finish(int o, int x, int pos, size_t idx, cx<R> v, R* a, R Pd, cx<R> accv) const {
+  __device__ void store_pre_k(int o, int x, int pos, cx<R> v, R* a, const unsigned char* src, cx<R> fin) const {
+    const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
+    finish(o, x, pos, idx, v, a, tor<R>(*reinterpret_cast<const double*>(src)),
+           *reinterpret_cast<const cx<R>*>(src + 8), fin);
+  }
+  __device__ __forceinline__ void finish(int o, int x, int pos, size_t idx, cx<R> v, R* a, R Pd, cx<R> accv,
+                                         cx<R> fv) const {
     R V;
     if constexpr (std::is_same<R, double>::value) {
       V = ph.gz2 * az.hxc2[pos] + (ph.gy2 * ay.hxc2[o] + ph.gx2 * ax.hxc2[x]);
@@ -831,7 +882,6 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
       const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
       V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
     }
-    const cx<R> fv = from64<R>(ldro(f + idx));
     const cx<R> pv = same ? fv : from64<R>(ldro(phi + idx));
     const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
     const cx<R> kin = add<R>(accv, v);

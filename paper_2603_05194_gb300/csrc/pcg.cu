@@ -54,7 +54,8 @@ struct Ctl {
   double Hpp, S1, S2, S3, curv, t0, t, pn, Aphiphi, Aphip, App, tolE;
   double cr, sr, nrm2, inv, En, linf, bestE, best_t;
   int accepted, nh, forced, pad1;
-  double inv0;  // normalisation of psi_0
+  double inv0;   // normalisation of psi_0
+  double noise;  // FP32 noise of the residual at phi_0 (automatic hand-over)
   // device-driven loop (Solver::run_device): the decisions the host takes
   // between iterations in the host-driven path, taken by control kernels
   int n, n_start, max_iter, max_halv;
@@ -62,7 +63,7 @@ struct Ctl {
   int logc, log_cap, f32, f32_iters;
   int total_h, f32_best_n, q, final_top;
   int step_logged, f32_window;
-  double tol_res, tol_linf, switch_tol, f32_best, linf_n;
+  double tol_res, tol_linf, switch_tol, f32_best, linf_n, f32_gain;
   unsigned long long deadline, guard, guard_max, launches;
   atkm_iter_log* log;  // device array of log_cap entries
 };
@@ -343,7 +344,8 @@ enum {
   S_T = SC_RED + 26,     // |phi+|^2 (+ unused)
   S_Q = SC_RED + 28,     // 2 quartic sums of phi+
   S_L = SC_RED + 30,     // linf
-  S_N = SC_RED + 31      // |psi0|^2
+  S_N = SC_RED + 31,     // |psi0|^2
+  S_Z = SC_RED + 32      // |H phi_0 in FP32 - H phi_0 in FP64|^2 (+ unused)
 };
 
 // ------------------------------------------------------------ control kernels
@@ -354,6 +356,10 @@ __global__ void k_c_init(Ctl* c, const double* s) {
   c->nan = !(n0 > 0.0) || !fin(n0);
   c->inv0 = c->nan ? 0.0 : 1.0 / n0;
 }
+
+// the FP32 arithmetic's noise in the residual at phi_0: ||H_32 phi_0 - H_64 phi_0||
+// (each with its own Phi), in the residual's norm
+__global__ void k_c_noise(Ctl* c, const double* s) { c->noise = sqrt(c->hv * s[S_Z]); }
 
 // loop top: energy terms of phi, mu, alpha (Step 2 and the shift of §2.3)
 __global__ void k_c_parts(Ctl* c, const double* s) {
@@ -499,10 +505,18 @@ __global__ void k_c_reset_state(Ctl* c, int have_E, int force_sd, int clear_prev
 // of a 256^3 multigrid solve 350 of them); 50 keeps the long bulk phases of
 // fast-rotating states within about 10% of their time.
 constexpr int kF32Window = 50;
+// Automatic hand-over (switch_tol < 0): the FP32 phase ends once its residual
+// is within kNoiseFactor of the FP32 noise measured at phi_0 (or at
+// |switch_tol|, whichever is larger), where its progress would stop; the floor
+// being detected that way, the stagnation window is only a backstop, long
+// enough not to end the slow, non-monotone progress of vortex-lattice states
+// (their residual can stay above its best for several hundred iterations).
+constexpr double kNoiseFactor = 4.0;
+constexpr int kF32WindowAuto = 2000;
 
 struct LoopInit {
   int n, max_iter, max_halv, caps, f32, log_cap, q, f32_window;
-  double tol_res, tol_linf, switch_tol, linf, time_limit_s;
+  double tol_res, tol_linf, switch_tol, linf, time_limit_s, f32_gain;
   atkm_iter_log* log;
   unsigned long long guard_max;
 };
@@ -529,6 +543,7 @@ __global__ void k_d_setup(Ctl* c, LoopInit L) {
   c->f32_best = INFINITY;
   c->q = L.q;
   c->f32_window = L.f32_window;
+  c->f32_gain = L.f32_gain;
   c->tol_res = L.tol_res;
   c->tol_linf = L.tol_linf;
   c->switch_tol = L.switch_tol;
@@ -559,7 +574,7 @@ __global__ void k_d_check(Ctl* c, cudaGraphConditionalHandle h_rest, int nodes) 
     c->status = ATKM_ERR_NAN;
     c->done = 1;
   } else {
-    if (c->f32 && c->res < 0.5 * c->f32_best) {
+    if (c->f32 && c->res < c->f32_gain * c->f32_best) {
       c->f32_best = c->res;
       c->f32_best_n = c->n;
     }
@@ -708,7 +723,7 @@ struct PcgBuffers {
   // resume state (host side)
   bool valid = false, f32 = false;
   int parity = 0, n = 0, caps = 0;
-  double linf = INFINITY;
+  double linf = INFINITY, sw_eff = 0.0;
   // device-driven solve graphs per [polish form][starts in FP32][start parity]
   cudaGraph_t dg[4][2][2] = {};
   cudaGraphExec_t dx[4][2][2] = {};
@@ -1177,6 +1192,8 @@ struct Solver {
   double eps_polish() const { return dwm ? epsdw : eps64; }
   std::chrono::steady_clock::time_point t_start;
   bool ran_device = false;
+  bool sw_auto = false;  // hand-over at the measured FP32 noise (switch_tol < 0)
+  double sw_eff = 0.0;   // the residual at which the FP32 phase hands over
 
   void chk(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
   double elapsed_s() const {
@@ -1186,7 +1203,10 @@ struct Solver {
 
   // ---- device-driven run (graphs on, profiling off)
   int fi_polish() const { return (split || dwm) ? (dwm ? 3 : 2) : 0; }
-  int f32_window() const { return opts->f32_window > 0 ? opts->f32_window : kF32Window; }
+  int f32_window() const {
+    return opts->f32_window > 0 ? opts->f32_window : (sw_auto ? kF32WindowAuto : kF32Window);
+  }
+  double f32_gain() const { return opts->f32_gain > 0.0 && opts->f32_gain < 1.0 ? opts->f32_gain : 0.5; }
   bool device_loop_ok() const { return use_graphs && B->graphs_ok && B->dl_ok && plan->prof == nullptr; }
   Seq seq_q(bool is32, int qq) {
     Seq S{plan, *B, ph, is32, qq};
@@ -1215,9 +1235,10 @@ struct Solver {
     I.log_cap = log_room();
     I.q = q;
     I.f32_window = f32_window();
+    I.f32_gain = f32_gain();
     I.tol_res = opts->tol_residual;
     I.tol_linf = opts->tol_linf;
-    I.switch_tol = opts->switch_tol;
+    I.switch_tol = sw_eff;
     I.linf = linf;
     I.time_limit_s = opts->time_limit_s > 0.0 ? std::max(opts->time_limit_s - elapsed_s(), 1e-9) : 0.0;
     I.log = B->dlog;
@@ -1342,6 +1363,8 @@ struct Solver {
     set_scalar(&B->ctl->beta, prm->beta);
     set_scalar(&B->ctl->lam, prm->lambda);
     f32 = mixed;
+    sw_auto = mixed && opts->switch_tol < 0.0;
+    sw_eff = fabs(opts->switch_tol);
     if (opts->resume && B->valid) {
       q = B->parity;
       n = n_start = f32_best_n = B->n;
@@ -1355,6 +1378,7 @@ struct Solver {
         f32 = false;
       } else {
         f32 = B->f32 && mixed;
+        if (f32 && sw_auto) sw_eff = std::max(sw_eff, B->sw_eff);
       }
       st = MAIN;
     } else {
@@ -1371,6 +1395,19 @@ struct Solver {
       S.atkm(SRC_PSI, reinterpret_cast<const double*>(B->phi[0]), nullptr, B->Phi[0]);
       S.ctl1(k_c_reset_state, B->ctl, 0, 1, 1);
       chk(S.err);
+      if (sw_auto) {
+        // the residual's FP32 noise at phi_0: H phi_0 with the FP32 operators
+        // (and the FP32 Phi_0 just formed) against binary64 throughout
+        Seq Z{plan, *B, ph, false, 0};
+        const double* p0d = reinterpret_cast<const double*>(B->phi[0]);
+        Z.atkm(SRC_PSI, p0d, nullptr, B->Phi1);
+        chk(launch_H<double>(plan, ph, p0d, p0d, B->Phi1, reinterpret_cast<double*>(B->Hp), -1, B->st));
+        chk(launch_H<float>(plan, ph, p0d, p0d, B->Phi[0], reinterpret_cast<double*>(B->Hphi), -1, B->st));
+        Z.lincomb(B->Pr, B->Hp, Coef{nullptr, 1.0}, B->Hphi, Coef{nullptr, -1.0}, nullptr, Coef{nullptr, 0.0},
+                  nullptr, S_Z, nullptr, false);
+        Z.ctl1(k_c_noise, B->ctl, (const double*)plan->scal);
+        chk(Z.err);
+      }
       fetch_async();
       st = INIT_CHECK;
     }
@@ -1430,6 +1467,7 @@ struct Solver {
           early_code = ATKM_ERR_NAN;
           st = DONE;
         } else {
+          if (sw_auto && isfinite(h.noise) && h.noise > 0.0) sw_eff = std::max(sw_eff, kNoiseFactor * h.noise);
           st = MAIN;
         }
         return;
@@ -1441,8 +1479,8 @@ struct Solver {
           ++logc;
         }
         if (h.nan) { status = ATKM_ERR_NAN; st = DONE; return; }
-        if (f32 && h.res < 0.5 * f32_best) { f32_best = h.res; f32_best_n = n; }
-        if (f32 && (h.res <= opts->switch_tol || caps >= 2 || n - f32_best_n > f32_window())) {
+        if (f32 && h.res < f32_gain() * f32_best) { f32_best = h.res; f32_best_n = n; }
+        if (f32 && (h.res <= sw_eff || caps >= 2 || n - f32_best_n > f32_window())) {
           // hand over to FP64: recompute Phi in FP64, re-evaluate this phi, restart the direction
           f32 = false;
           caps = 0;
@@ -1510,7 +1548,7 @@ struct Solver {
     Ctl& h = H();
     B->valid = (status == ATKM_OK || status == ATKM_NOT_CONVERGED || status == ATKM_STAGNATED ||
                 status == ATKM_ERR_TIMEOUT);
-    B->f32 = f32; B->parity = q; B->n = n; B->caps = caps; B->linf = linf;
+    B->f32 = f32; B->parity = q; B->n = n; B->caps = caps; B->linf = linf; B->sw_eff = sw_eff;
     chk(cudaMemcpyAsync(psi, B->phi[q], B->N * sizeof(double2), cudaMemcpyDeviceToDevice, B->st));
     chk(cudaEventRecord(B->ev_out, B->st));
     chk(cudaStreamWaitEvent(caller, B->ev_out, 0));
@@ -1535,6 +1573,7 @@ struct Solver {
     out->status = status;
     out->log_count = logc;
     out->device_loop = ran_device ? 1 : 0;
+    out->switch_residual = mixed ? sw_eff : 0.0;
     if (status != ATKM_OK) {
       const char* why = status == ATKM_NOT_CONVERGED ? "max_iter reached"
                         : status == ATKM_STAGNATED   ? "three consecutive exhausted halving loops"
@@ -1745,6 +1784,7 @@ int pcg_ground_state_mg(int levels, atkm_plan* const* plans, const atkm_params* 
       const double used = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       o.time_limit_s = std::max(opts->time_limit_s - used, 1e-9);
     }
+    o.precision_mode = i < opts->mg_f64_levels ? ATKM_PRECISION_F64 : opts->precision_mode;
     code = pcg_ground_state(plans[i], prm, &o, psi[i], &out[i], stream);
     if (code != ATKM_OK && code != ATKM_NOT_CONVERGED && code != ATKM_STAGNATED) return code;
     if (i + 1 < levels) {

@@ -438,7 +438,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   if (!isfinite(nn) || fabs(nn - 1.0) > 1e-12)
     return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: dipole axis must be a unit vector (| |n|-1 | <= 1e-12)");
-  if (flags & ~(unsigned)(ATKM_PLAN_F32 | ATKM_PLAN_DF32 | ATKM_PLAN_GENERIC_FFT))
+  if (flags & ~(unsigned)(ATKM_PLAN_F32 | ATKM_PLAN_DF32 | ATKM_PLAN_GENERIC_FFT | ATKM_PLAN_AUTOTUNE))
     return fail(nullptr, ATKM_ERR_ARG, "atkm_plan_create: unknown flags");
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -450,6 +450,7 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   p->W1 = p->W2 = p->T1 = nullptr;
   p->W1f = p->W2f = p->T1f = nullptr; p->partials = nullptr; p->scal = nullptr; p->scal_host = nullptr;
   p->pcg = nullptr; p->prof = nullptr; p->prof_stopped_ = nullptr; p->bytes = 0; p->flags = flags;
+  p->n_tune = 0;
   Geo& g = p->g;
   g.Nx = N[0]; g.Ny = N[1]; g.Nz = N[2];
   g.Mx = 2 * N[0]; g.My = 2 * N[1]; g.Mz = 2 * N[2];
@@ -602,6 +603,14 @@ int atkm_plan_create(atkm_plan** out, const int N[3], const double L[3], const d
   if ((e = cudaMallocHost((void**)&p->scal_host, SC_COUNT * sizeof(double))) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan scalars"));
   if ((e = cudaMemsetAsync(p->scal, 0, SC_COUNT * sizeof(double), st)) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan scalars"));
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(nullptr, e, "plan create"));
+  if (flags & ATKM_PLAN_AUTOTUNE) {
+    const int code = atkm_plan_autotune(p, stream);
+    if (code != ATKM_OK) {
+      const std::string msg = p->err;
+      bail(code);
+      return fail(nullptr, code, msg);
+    }
+  }
   *out = p;
   return ATKM_OK;
 }

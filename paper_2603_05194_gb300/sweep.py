@@ -2,10 +2,13 @@
 
 Every instance is its own Algorithm 1 run (own plan, own multiplier K, own
 state); pcg_ground_state_batched builds all of them into one CUDA graph and
-launches it once.  This module times that call against the same instances
-solved one after another, and runs the sweep to the residual tolerance (in
-one launch, double-word split form), optionally against each instance solved
-alone in binary64.  It only orders calls and keeps the books.
+launches it once.  The plans are autotuned (atkm_plan_autotune: the FFT
+engine and tile of every non-power-of-two line length picked by timing).
+This module times that call against the same instances solved one after
+another (and against untuned plans), and runs the sweep to the residual
+tolerance (in one launch, double-word split form), optionally against each
+instance solved alone in binary64.  It only orders calls and keeps the
+books.
 """
 from __future__ import annotations
 
@@ -28,30 +31,47 @@ def _timed(fn):
 
 
 def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PRECISION_F32_F64, B.PRECISION_F64),
-        log=print, reference=False):
-    plans = [B.Plan(p.N, p.L, p.n, f32=True, df32=True) for p in problems]
+        log=print, reference=False, autotune=True):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plans = [B.Plan(p.N, p.L, p.n, f32=True, df32=True, autotune=autotune) for p in problems]
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
     prms = [B.make_params(p.gamma, p.beta, p.lam, p.Omega) for p in problems]
 
     def psis():
         return [torch.from_numpy(psi0_fn(p)).cuda() for p in problems]
 
-    out = dict(instances=len(problems), grids=[list(p.N) for p in problems], fixed_iters=iters)
+    out = dict(instances=len(problems), grids=[list(p.N) for p in problems], fixed_iters=iters, autotune=autotune,
+               plan_create_s=tune_s)
+    if autotune:
+        tun = [t for pl in plans for t in pl.tuning()]
+        out["tuning"] = dict(entries=len(tun), changed=sum(1 for t in tun if t["ms_best"] < t["ms_default"]),
+                             mixed_radix=sum(1 for t in tun if t["engine"] == 1),
+                             narrowed_tiles=sum(1 for t in tun if t["engine"] == 2 and t["tile_shift"] > 0),
+                             ms_default=sum(t["ms_default"] for t in tun), ms_best=sum(t["ms_best"] for t in tun))
+        log(f"autotuned {len(plans)} plans in {tune_s:.1f} s (plan creation included): {out['tuning']}")
+    untuned = [B.Plan(p.N, p.L, p.n, f32=True, df32=True) for p in problems] if autotune else None
     try:
         for prec in precisions:
             name = "mixed" if prec == B.PRECISION_F32_F64 else "f64"
-            ps = psis()
-            B.pcg_ground_state_batched(plans, prms, ps, max_iter=3, precision=prec)  # capture graphs
-            ps = psis()
-            _, tb = _timed(lambda: B.pcg_ground_state_batched(plans, prms, ps, max_iter=iters, tol_residual=0.0,
-                                                              precision=prec))
+            arms = [("", plans)] + ([("untuned_", untuned)] if untuned else [])
+            for label, pls in arms:
+                ps = psis()
+                B.pcg_ground_state_batched(pls, prms, ps, max_iter=3, precision=prec)  # capture graphs
+                ps = psis()
+                _, tb = _timed(lambda: B.pcg_ground_state_batched(pls, prms, ps, max_iter=iters, tol_residual=0.0,
+                                                                  precision=prec))
+                out[f"{name}_{label}batched_s"] = tb
             ps = psis()
             _, ts = _timed(lambda: [pl.pcg_ground_state(pr, p, max_iter=iters, tol_residual=0.0, precision=prec)
                                     for pl, pr, p in zip(plans, prms, ps)])
-            out[f"{name}_batched_s"] = tb
+            tb = out[f"{name}_batched_s"]
             out[f"{name}_sequential_s"] = ts
             out[f"{name}_instance_iters_per_s_batched"] = len(problems) * iters / tb
             log(f"{name}: {iters} iterations x {len(problems)} instances: batched {tb:.3f} s, "
-                f"one by one {ts:.3f} s ({ts / tb:.2f}x)")
+                f"one by one {ts:.3f} s ({ts / tb:.2f}x)" +
+                (f", batched on untuned plans {out[f'{name}_untuned_batched_s']:.3f} s" if untuned else ""))
         if full_iters > 0:
             # the sweep to the tolerance: all instances in one graph launch
             # (double-word split form) against each instance alone in binary64
@@ -82,7 +102,7 @@ def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PR
                     f"{out['reference_f64_one_by_one']['lower_energy_batched']} lower, "
                     f"{out['reference_f64_one_by_one']['higher_energy_batched']} higher of {len(both)}")
     finally:
-        for pl in plans:
+        for pl in plans + (untuned or []):
             pl.close()
     return out
 
@@ -94,15 +114,20 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--full-iters", type=int, default=3000, help="0 skips the run to the tolerance")
     ap.add_argument("--reference", action="store_true", help="also solve each instance alone in binary64")
+    ap.add_argument("--no-autotune", action="store_true", help="plans with the fixed engine rule")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     B.load_library()
-    res = run(W.sweep_instances(a.count), W.initial_guess, a.iters, a.full_iters, reference=a.reference)
+    res = run(W.sweep_instances(a.count), W.initial_guess, a.iters, a.full_iters, reference=a.reference,
+              autotune=not a.no_autotune)
     js = json.dumps(res)
     if a.out:
         with open(a.out, "w") as fh:
             fh.write(js + "\n")
     print(json.dumps({k: v for k, v in res.items() if k not in ("grids", "full", "reference_f64_one_by_one")}))
+    if "full" in res:
+        f = res["full"]
+        print(json.dumps({"full": {k: f[k] for k in ("tol", "max_iter", "seconds", "statuses", "device_loop")}}))
 
 
 if __name__ == "__main__":

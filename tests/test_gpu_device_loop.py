@@ -35,13 +35,15 @@ def _solve(lib, plan, w, precision, mode, max_iter=600, **kw):
     return r, psi.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2, 3])
-def test_device_loop_equals_host_loop(lib, precision):
+@pytest.mark.parametrize("precision,kw", [(0, {}), (1, {}), (2, {}), (3, {}), (1, dict(f32_gain=0.9, f32_window=5)),
+                                          (3, dict(switch_tol=-1e-5))])
+def test_device_loop_equals_host_loop(lib, precision, kw):
     """Full solves of the 32x32x16 workload in every precision form (the
-    FP32 forms hand over to their polish on the device)."""
+    FP32 forms hand over to their polish on the device), and with another
+    FP32 stagnation rule (progress factor 0.9 within 5 iterations)."""
     w = W.CONFIGS["cfg1_32x32x16"]
     plan = lib.Plan(w.N, w.L, w.n, f32=precision != 0, df32=precision == 3)
-    runs = {m: _solve(lib, plan, w, precision, m) for m in ("graph", "direct", "profiled")}
+    runs = {m: _solve(lib, plan, w, precision, m, **kw) for m in ("graph", "direct", "profiled")}
     rg, pg = runs["graph"]
     assert rg["status_name"] == "OK"
     assert rg["device_loop"] == 1 and runs["direct"][0]["device_loop"] == 0 and runs["profiled"][0]["device_loop"] == 0
@@ -121,3 +123,29 @@ def test_batched_single_launch_equals_single_solves_with_handover(lib):
         assert o["iters"] == ref["iters"] and o["f32_iters"] == ref["f32_iters"] > 0
         assert o["E"] == ref["E"]
         assert np.array_equal(ps.cpu().numpy(), ref_psi)
+
+
+def test_automatic_handover_at_fp32_noise(lib):
+    """switch_tol < 0: the FP32 phase hands over at the larger of |switch_tol|
+    and 4x the residual's FP32 noise measured at phi_0; that noise is the
+    level at which an FP32 phase that never hands over stops making progress
+    (its residual floor), within a factor of 10."""
+    w = W.CONFIGS["cfg1_32x32x16"]
+    plan = lib.Plan(w.N, w.L, w.n, f32=True)
+    prm = lib.make_params(w.gamma, w.beta, w.lam, w.Omega)
+    r = plan.pcg_ground_state(prm, dev(W.initial_guess(w)), max_iter=3000, precision=1, switch_tol=-1e-12,
+                              log_capacity=3002)
+    sw = r["switch_residual"]
+    assert r["status_name"] == "OK" and r["f32_iters"] > 0 and sw > 1e-12
+    f32_log = [e for e in r["log"] if e["f32_phase"]]
+    assert all(e["residual"] > sw for e in f32_log)
+    noise = sw / 4.0
+    # the same start in FP32 only: its residual floor
+    q = plan.pcg_ground_state(prm, dev(W.initial_guess(w)), max_iter=len(f32_log) + 400, tol_residual=0.0,
+                              precision=1, switch_tol=1e-14, f32_window=10 ** 8, log_capacity=4000)
+    res = [e["residual"] for e in q["log"] if e["f32_phase"]]
+    floor = min(res)
+    assert floor / 10 <= noise <= 10 * floor, (noise, floor)
+    # a plain switch_tol reports itself
+    r2 = plan.pcg_ground_state(prm, dev(W.initial_guess(w)), max_iter=3000, precision=1, switch_tol=1e-5)
+    assert r2["switch_residual"] == 1e-5

@@ -48,3 +48,24 @@ def test_mg_rejects_bad_levels(lib):
         lib.pcg_ground_state_mg([p1, p0], prm, [a, b], max_iter=2)   # coarser
     with pytest.raises(lib.AtkmError):
         lib.pcg_ground_state_mg([p1, p1], prm, [a, a], max_iter=2)   # same plan
+
+
+def test_mg_f64_levels(lib):
+    """mg_f64_levels: with a precision form, the coarsest levels run in FP64
+    (bitwise the FP64 cascade's levels, no FP32 iterations there), the rest in
+    the form; every level ends at the oracle's energy."""
+    prm = lib.make_params(GAMMA, 50.0, 15.0, 0.4)
+
+    def run(precision, **kw):
+        plans = [lib.Plan(N, L, NAX, f32=True) for N in GRIDS]
+        psis = [torch.from_numpy(W.guess_phi_d(GRIDS[0], L, GAMMA, 0.4)).cuda()] + \
+               [torch.zeros(p.shape, dtype=torch.complex128, device="cuda") for p in plans[1:]]
+        return lib.pcg_ground_state_mg(plans, prm, psis, tol_residual=1e-9, max_iter=400, precision=precision,
+                                       **kw), psis
+
+    f64, p64 = run(0)
+    mix, pmix = run(1, mg_f64_levels=2)
+    assert [r["f32_iters"] for r in mix][:2] == [0, 0] and mix[2]["f32_iters"] > 0
+    for i in range(2):
+        assert torch.equal(p64[i], pmix[i]) and mix[i]["E"] == f64[i]["E"] and mix[i]["iters"] == f64[i]["iters"]
+    assert mix[2]["status_name"] == "OK" and abs(mix[2]["E"] - f64[2]["E"]) <= 1e-10 * abs(f64[2]["E"])
