@@ -517,13 +517,23 @@ template <typename R> inline const TuneEntry* tuned(const atkm_plan* p, int L, b
   return nullptr;
 }
 
+// Lengths the mixed-radix register engine is instantiated for in arithmetic
+// R (run_pass's switches): 3 * 2^a and 5 * 2^a in FP32, 3 * 2^a in binary64,
+// none in double-word.  Both the fixed rule and the autotuner go through this.
+template <typename R> inline bool mix_ok(int L) {
+  if (std::is_same<R, df>::value || !mix_len(L)) return false;
+  return !(std::is_same<R, double>::value && L % 5 == 0);
+}
+inline bool mix_ok_r(int r, int L) {
+  return r == 0 ? mix_ok<double>(L) : (r == 1 ? mix_ok<float>(L) : mix_ok<df>(L));
+}
+
 template <typename R> inline PassGrid pass_grid(const atkm_plan* p, int L, bool LM, long lines, int X, int outer) {
   PassGrid pg;
   pg.fast = fast_len(L);
-  pg.mix = !pg.fast && !std::is_same<R, df>::value && !(p->flags & ATKM_PLAN_GENERIC_FFT) && mix_len(L) &&
-           !(std::is_same<R, double>::value && L % 5 == 0);
+  pg.mix = !pg.fast && !(p->flags & ATKM_PLAN_GENERIC_FFT) && mix_ok<R>(L);
   const TuneEntry* te = pg.fast ? nullptr : tuned<R>(p, L, LM);
-  if (te) pg.mix = te->mix != 0 && mix_len(L) && !std::is_same<R, df>::value;
+  if (te) pg.mix = te->mix != 0 && mix_ok<R>(L);
   if (pg.fast) pg.T = kFastElems / L;
   else if (pg.mix) pg.T = kThreads / (L / (L % 3 == 0 ? 12 : 20));
   else {
@@ -584,7 +594,8 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
         case 160: return launch_mix_L<R, 160>(op, f, pg, st);
         case 192: return launch_mix_L<R, 192>(op, f, pg, st);
         case 320: return launch_mix_L<R, 320>(op, f, pg, st);
-        default: return launch_mix_L<R, 384>(op, f, pg, st);
+        case 384: return launch_mix_L<R, 384>(op, f, pg, st);
+        default: return cudaErrorInvalidValue;
       }
     }
   } else if constexpr (std::is_same<R, double>::value) {
@@ -594,7 +605,8 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
         case 48: return launch_mix_L<R, 48>(op, f, pg, st);
         case 96: return launch_mix_L<R, 96>(op, f, pg, st);
         case 192: return launch_mix_L<R, 192>(op, f, pg, st);
-        default: return launch_mix_L<R, 384>(op, f, pg, st);
+        case 384: return launch_mix_L<R, 384>(op, f, pg, st);
+        default: return cudaErrorInvalidValue;
       }
     }
   }
@@ -606,7 +618,8 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
       case 128: return launch_fast_L<R, 128>(op, f, pg, st);
       case 256: return launch_fast_L<R, 256>(op, f, pg, st);
       case 512: return launch_fast_L<R, 512>(op, f, pg, st);
-      default: return launch_fast_L<R, 1024>(op, f, pg, st);
+      case 1024: return launch_fast_L<R, 1024>(op, f, pg, st);
+      default: return cudaErrorInvalidValue;
     }
   }
   static std::atomic<unsigned long long> prepared{0};

@@ -7,7 +7,8 @@
 // of two, per arithmetic the plan carries (binary64, and FP32 / double-word
 // with ATKM_PLAN_F32 / ATKM_PLAN_DF32) and per layout (the line-major x pass,
 // the strided y and z passes).  Candidates: the mixed-radix register engine
-// (lengths 3 * 2^a and 5 * 2^a up to 384; not for double-word) and the
+// where run_pass instantiates it (3 * 2^a and 5 * 2^a up to 384 in FP32,
+// 3 * 2^a in binary64, none in double-word) and the
 // generic engine at its default tile width, half of it and a quarter of it.
 // Each candidate is timed on the plan's own operators -- the ATKM of |psi|^2,
 // H psi and P r (no preconditioner in double-word) -- with CUDA events, the
@@ -77,7 +78,7 @@ cudaError_t time_ops(atkm_plan* p, int r, const Phys& ph, const Scratch& s, cuda
 }
 
 bool default_mix(const atkm_plan* p, int r, int L) {
-  return r != 2 && !(p->flags & ATKM_PLAN_GENERIC_FFT) && mix_len(L) && !(r == 0 && L % 5 == 0);
+  return !(p->flags & ATKM_PLAN_GENERIC_FFT) && mix_ok_r(r, L);
 }
 
 }  // namespace
@@ -125,7 +126,7 @@ int atkm_plan_autotune(atkm_plan* plan, void* stream) {
         seen = seen || (plan->tune[i].r == r && plan->tune[i].L == L && plan->tune[i].lm == lm);
       if (seen || plan->n_tune >= kMaxTune) continue;
       std::vector<std::pair<int, int>> cand;
-      if (r != 2 && !(plan->flags & ATKM_PLAN_GENERIC_FFT) && mix_len(L)) cand.push_back({1, 0});
+      if (!(plan->flags & ATKM_PLAN_GENERIC_FFT) && mix_ok_r(r, L)) cand.push_back({1, 0});
       for (int sh = 0; sh <= 2; ++sh) cand.push_back({0, sh});
       TuneEntry& te = plan->tune[plan->n_tune++];
       te.r = r;
