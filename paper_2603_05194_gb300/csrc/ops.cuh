@@ -116,7 +116,11 @@ template <int L> struct FastCfg {
 
 template <typename R, int L> struct FastSmem {
   static constexpr int buf = kFastElems + (kFastElems >> SmemShift<R>::value) + 1;
-  static constexpr size_t bytes = (size_t)(L + 2 * buf) * sizeof(cx<R>);
+  // stage s exchanges through b0 (s even) or b1 (s odd) unless it is the last
+  // stage; with one or two radix-8 stages and nothing after them (L <= 64)
+  // only b0 is used, so b1 takes no shared memory
+  static constexpr bool kTwoBufs = FastCfg<L>::A == 3 || (FastCfg<L>::A == 2 && FastCfg<L>::REM > 1);
+  static constexpr size_t bytes = (size_t)(L + (kTwoBufs ? 2 : 1) * buf) * sizeof(cx<R>);
 };
 
 template <typename R, int L, bool LM> __device__ __forceinline__ int fsa(int t, int pos) {
@@ -304,15 +308,17 @@ __device__ __forceinline__ void reduce_out(R (&acc)[NR], double* part, int pstri
   }
 }
 
-// CTAs per SM the fast engine is compiled for: 4 in FP32 (64 registers), 3
-// when the prefetch buffer of 16 bytes an element already limits the shared
-// memory to 3 CTAs (80 registers), 2 otherwise (128 registers).
-template <typename R, class Op> constexpr int fast_min_blocks() {
-  return sizeof(R) == 4 ? (Op::kPre >= 16 ? 3 : 4) : 2;
+// CTAs per SM the fast engine is compiled for: 4 in FP32 (64 registers); 3
+// (80 registers) with a prefetch buffer of 16 bytes an element, when two
+// exchange buffers already limit the shared memory to 3 CTAs, and for
+// L < 64, whose instances spill 8-88 bytes at 64 registers (L = 64: 4 bytes);
+// 2 otherwise (128 registers).
+template <typename R, int L, class Op> constexpr int fast_min_blocks() {
+  return sizeof(R) == 4 ? (Op::kPre >= 16 && (FastSmem<R, L>::kTwoBufs || L < 64) ? 3 : 4) : 2;
 }
 
 template <typename R, int L, class Op>
-__global__ void __launch_bounds__(kThreads, fast_min_blocks<R, Op>()) k_fast(Op op, const cx<R>* __restrict__ twg) {
+__global__ void __launch_bounds__(kThreads, fast_min_blocks<R, L, Op>()) k_fast(Op op, const cx<R>* __restrict__ twg) {
   using C = FastCfg<L>;
   extern __shared__ __align__(16) unsigned char fast_smem[];
   cx<R>* tw = reinterpret_cast<cx<R>*>(fast_smem);
