@@ -65,11 +65,15 @@ def parse():
     ap.add_argument("--ttt", default="f64,f32_f64,df32_split,df32_split_all",
                     help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split; "
                          "a form runs on the finest level, or on every level with the suffix _all)")
+    ap.add_argument("--case", choices=["step", "sweep"], default="step",
+                    help="step: the PCG step on 256x256x64 (default); sweep: the 48-instance uneven-grid sweep to "
+                         "residual 1e-8 (batched vs one by one), one JSON line")
+    ap.add_argument("--sweep-max-iter", type=int, default=12000, help="iteration cap of each sweep instance")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
                                                "profiling_overhead", "polish_df32", "fp64_peak", "iterations",
                                                "virial_vs_tol", "engines", "finest_level", "basin",
-                                               "f32_floor", "mg_policy"],
+                                               "f32_floor", "mg_policy", "guess_gemm"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture, or one of the "
                          "timings quoted in the design notes, and exit")
     a = ap.parse_args()
@@ -679,6 +683,35 @@ def study_case(case: str):
         p.close()
 
 
+def guess_gemm_case():
+    """guess_gemm: one training step of the learned-guess network at batch 32
+    (seeded random features and targets), its GEMMs bracketed by CUDA events,
+    on each dense-GEMM engine (tcgen05 with the accumulator in tensor memory,
+    and the warp-level mma.sync kernel): per-GEMM milliseconds in launch order
+    (the five forward layers, then per layer from the last the weight and the
+    input gradient), the GEMM share of the step, best of 20 steps after 5."""
+    import numpy as np
+    import torch
+    from paper_2603_05194_gb300 import binding as B
+    rng = np.random.default_rng(11)
+    f = torch.from_numpy(rng.uniform(-1, 1, size=(32, 8)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((32,) + B.GUESS_SHAPE) +
+                         1j * rng.standard_normal((32,) + B.GUESS_SHAPE)).cuda()
+    row = {"case": "guess_gemm", "batch": 32}
+    for name, eng in (("tcgen05", B.ATKM_GEMM_TCGEN05), ("mma_sync", B.ATKM_GEMM_MMA_SYNC)):
+        net = B.GuessNet(seed=1)
+        net.set_gemm_engine(eng)
+        for _ in range(5):
+            net.profile_step(f, t, 1e-4)
+        runs = [net.profile_step(f, t, 1e-4) for _ in range(20)]
+        net.check()
+        best = min(runs, key=lambda r: r["step_ms"])
+        row[name] = {"step_ms": round(best["step_ms"], 4), "gemm_ms": round(best["gemm_ms"], 4),
+                     "gemm_share": round(best["gemm_ms"] / best["step_ms"], 3),
+                     "each_ms": [round(x, 4) for x in best["each_ms"]]}
+    print(json.dumps(row), flush=True)
+
+
 def engines_case():
     """engines: the FFT engines on the grids of the uneven-grid sweep
     (edge e in-plane, e/4 along z, box of the sweep): stand-alone ATKM and
@@ -884,6 +917,9 @@ def profile_case(case: str):
     if case in ("finest_level", "basin", "f32_floor", "mg_policy"):
         forms_case(case)
         return
+    if case == "guess_gemm":
+        guess_gemm_case()
+        return
     if case == "fp64_peak":
         from paper_2603_05194_gb300 import binding as B
         runs = [B.measure_fp64_fma(blocks_per_sm=b, iters=4096, repeats=5) for b in (4, 8, 16)]
@@ -910,6 +946,39 @@ def profile_case(case: str):
         print(case, r["status_name"], r["iters"], r["E"])
 
 
+def sweep_line(args):
+    """The batched uneven-grid sweep (48 instances, grids 64x64x16 ... 192x192x48,
+    autotuned plans) to residual 1e-8: value = seconds of the one-launch
+    batched solve in the double-word split form (FP32 bulk); beside it the
+    same launch in binary64 and every instance solved alone in binary64, one
+    after another, with the energies compared instance by instance."""
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+    from paper_2603_05194_gb300 import sweep as S
+    B.load_library()
+    torch.cuda.set_device(0)
+    probs = W.sweep_instances(48)
+    n0 = B.launch_count()
+    out = S.to_tolerance(probs, W.initial_guess, max_iter=args.sweep_max_iter, tol=TOL,
+                         log=lambda m: print(m, file=sys.stderr, flush=True))
+    launches = B.launch_count() - n0
+    main = out["df32_split_batched"]
+    line = {"metric": "uneven-grid sweep time to residual 1e-8 (48 instances, one graph launch)",
+            "value": round(main["seconds"], 3), "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": round(main["seconds"] * 1e3, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+df32+f64", "data": "synthetic",
+            "config": {"workload": "sweep48_uneven_64x64x16_to_192x192x48", "tol": TOL,
+                       "max_iter": args.sweep_max_iter, "grids": out["grids"], "autotune": True},
+            "gpu_launches": launches,
+            "gpu_launches_note": "the library's kernels executed in the three solves (inside the device-driven "
+                                 "graphs the control kernels count the nodes of every body they run)",
+            "tuning": out.get("tuning"),
+            "forms": {k: out[k] for k in ("f64_one_by_one", "f64_batched",
+                                                                     "df32_split_batched")}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.cpu_sample:
@@ -917,6 +986,9 @@ def main():
         return
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.case == "sweep":
+        sweep_line(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

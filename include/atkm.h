@@ -410,7 +410,11 @@ int pcg_ground_state_mg(int levels, atkm_plan* const* plans, const atkm_params* 
  * 4x8x8 voxels x 32 channels -> transposed 3D convolutions with kernel =
  * stride: 32 -> 16 ch (stride 2, ReLU), 16 -> 8 (stride 2, ReLU), 8 -> 2
  * (stride (1,2,2); Re, Im).  Every layer runs as a GEMM with BF16 operands
- * and FP32 accumulation on the tensor cores; parameters are FP32 (master
+ * and FP32 accumulation: the MLP layers and their gradients on the tcgen05
+ * tensor cores (accumulator in tensor memory; engine selectable with
+ * atkm_guess_net_set_gemm_engine), the transposed convolutions, whose
+ * products need at most 4096 weights a row, on the CUDA cores (they are
+ * bound by memory traffic, not multiply-adds); parameters are FP32 (master
  * copy) and trained with Adam on the loss 1 - |<u,t>|^2/(|u|^2 |t|^2) (mean
  * over the batch), which ignores the global phase and scale of the targets.
  *   feats    device, batch x 8 floats.
@@ -431,6 +435,18 @@ int atkm_guess_net_grad(atkm_guess_net* net, int batch, const float* feats, cons
                         float* grad_out, float* loss, void* stream);
 int atkm_guess_net_train_step(atkm_guess_net* net, int batch, const float* feats, const double* targets,
                               float lr, float* loss, void* stream);
+/* Engine of the network's dense GEMMs: ATKM_GEMM_TCGEN05 (default; tcgen05.mma
+ * with the accumulator in tensor memory, 128-row tiles) or ATKM_GEMM_MMA_SYNC
+ * (warp-level mma.sync m16n8k16, kept for comparison).  Both round the
+ * operands to BF16 and sum in FP32.  ATKM_ERR_ARG for another value.
+ * Implementation choice; the paper has no counterpart. */
+#define ATKM_GEMM_TCGEN05 0
+#define ATKM_GEMM_MMA_SYNC 1
+int atkm_guess_net_set_gemm_engine(atkm_guess_net* net, int engine);
+/* Synchronises `stream` and reports whether any tcgen05 GEMM of this network
+ * gave up a bounded wait for its MMAs since the last check (ATKM_ERR_TIMEOUT;
+ * that GEMM's output is then not written), else ATKM_OK.  Clears the flag. */
+int atkm_guess_net_check(atkm_guess_net* net, void* stream);
 /* One training step as atkm_guess_net_train_step, with every GEMM bracketed by
  * CUDA events on `stream`: *gemm_ms = their summed time, *step_ms = the whole
  * step, *gemm_calls = the GEMMs timed, each_ms[i] (if not NULL, up to

@@ -33,6 +33,8 @@ PRECISION_F64 = 0
 PRECISION_F32_F64 = 1
 PRECISION_F32_SPLIT = 2
 PRECISION_DF32_SPLIT = 3
+ATKM_GEMM_TCGEN05 = 0
+ATKM_GEMM_MMA_SYNC = 1
 
 
 class AtkmError(RuntimeError):
@@ -122,6 +124,8 @@ def load_library(path: str = LIB_PATH):
         "atkm_guess_net_forward": (ip, [vp, C.c_int, vp, vp, vp]),
         "atkm_guess_net_grad": (ip, [vp, C.c_int, vp, vp, vp, vp, vp]),
         "atkm_guess_net_train_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, vp]),
+        "atkm_guess_net_set_gemm_engine": (ip, [vp, C.c_int]),
+        "atkm_guess_net_check": (ip, [vp, vp]),
         "atkm_guess_net_profile_step": (ip, [vp, C.c_int, vp, vp, C.c_float, vp, dp, dp, C.POINTER(C.c_int), dp,
                                              C.c_int, vp]),
         "atkm_plan_set_profiling": (ip, [vp, C.c_int]),
@@ -256,6 +260,14 @@ class GuessNet:
     def _check(self, code):
         if code != ATKM_OK:
             raise AtkmError(code, self._lib.atkm_last_error_string(None).decode())
+
+    def set_gemm_engine(self, engine: int):
+        """ATKM_GEMM_TCGEN05 (default) or ATKM_GEMM_MMA_SYNC for the dense GEMMs."""
+        self._check(self._lib.atkm_guess_net_set_gemm_engine(self._h, int(engine)))
+
+    def check(self, stream=None):
+        """Raises ATKM_ERR_TIMEOUT if a tensor-core GEMM gave up waiting (synchronises the stream)."""
+        self._check(self._lib.atkm_guess_net_check(self._h, _stream(stream)))
 
     def get_params(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")

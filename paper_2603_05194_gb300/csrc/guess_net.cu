@@ -8,8 +8,12 @@
 //   L3: 8 -> 2 (Re, Im), stride (1,2,2).
 // Activations stay in GEMM row order (row = voxel, column = sub-position x
 // channel); only the final output is mapped to the (z, y, x) grid.  Every
-// layer is a GEMM with BF16 operands and FP32 accumulation on the tensor cores
-// (warp-level mma m16n8k16); weights have FP32 master copies updated by Adam.
+// layer is a GEMM with BF16 operands and FP32 accumulation: the dense ones
+// (the MLP and its gradients) on the tcgen05 tensor cores with the
+// accumulator in tensor memory (tc_gemm.cuh; the warp-level mma m16n8k16
+// kernel is kept as a selectable alternative), the skinny transposed-
+// convolution products on the CUDA cores (memory-bound; see below); weights
+// have FP32 master copies updated by Adam.
 // Loss per sample (phase and scale invariant, so targets defined up to a
 // global phase are learnable): L = 1 - |<u,t>|^2 / (|u|^2 |t|^2).
 #include <cuda_bf16.h>
@@ -20,6 +24,7 @@
 #include <vector>
 
 #include "atkm_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace atkm {
 namespace {
@@ -439,6 +444,8 @@ int ew_grid(long n) {
 using namespace atkm;
 
 struct atkm_guess_net {
+  int gemm_engine = ATKM_GEMM_TCGEN05;  // dense GEMMs: tcgen05 or the warp-level mma.sync kernel
+  unsigned* tc_err = nullptr;  // device flag: a tensor-core wait gave up (atkm_guess_net_check)
   float* w = nullptr;   // FP32 master parameters
   float* g = nullptr;   // gradients
   float* m = nullptr;   // Adam moments
@@ -497,6 +504,77 @@ struct GemmTimer {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
 thread_local GemmTimer* g_gemm_timer = nullptr;
+// the calling network's engine and error flag, set on entry of each call
+thread_local int g_gemm_engine = ATKM_GEMM_TCGEN05;
+thread_local unsigned* g_tc_err = nullptr;
+
+struct EngineScope {
+  int e0;
+  unsigned* f0;
+  explicit EngineScope(const atkm_guess_net* n) : e0(g_gemm_engine), f0(g_tc_err) {
+    g_gemm_engine = n->gemm_engine;
+    g_tc_err = n->tc_err;
+  }
+  ~EngineScope() {
+    g_gemm_engine = e0;
+    g_tc_err = f0;
+  }
+};
+
+template <int BN>
+cudaError_t launch_tc(dim3 grid, const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C,
+                      long scm, long scn, int M, int N, int K, int kchunk, cudaStream_t st) {
+  // dynamic shared memory above 48 KB is opted into once per device
+  static std::atomic<unsigned long long> prepared{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(prepared.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(tc::k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::Cfg<BN>::kSmem);
+    if (e != cudaSuccess) return e;
+    prepared.fetch_or(bit, std::memory_order_acq_rel);
+  }
+  tc::k_gemm_tc<BN><<<grid, tc::kThreads, tc::Cfg<BN>::kSmem, st>>>(A, sam, sak, Bm, sbk, sbn, C, scm, scn, M, N, K,
+                                                                      kchunk, g_tc_err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// C = A B on the tcgen05 path.  Tiles are 128 rows of the computed product,
+// one row per tensor-memory lane and so per thread of the epilogue.  The
+// product is computed transposed (C^T = B^T A^T, stored through C's strides)
+// unless C has at least 128 rows and fewer columns than rows: the lanes then
+// run along C's contiguous rows, so each warp's stores are coalesced, and
+// the batch dimension (32) of the MLP products becomes the tile width.  K is
+// split over CTAs (atomic adds into a zeroed C) when split_k allows it and
+// the tiles alone would not fill the SMs.
+cudaError_t gemm_tc(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc, int M,
+                    int N, int K, cudaStream_t st, bool split_k) {
+  const bool tr = M < tc::kM || N >= M;
+  const float* Ap = tr ? Bm : A;
+  const float* Bp = tr ? A : Bm;
+  const long asm_ = tr ? sbn : sam, ask = tr ? sbk : sak;  // A'(m, k)
+  const long bsk = tr ? sak : sbk, bsn = tr ? sam : sbn;   // B'(k, n)
+  const long scm = tr ? 1 : ldc, scn = tr ? ldc : 1;
+  const int Mm = tr ? N : M, Nn = tr ? M : N;
+  const int BN = Nn <= 32 ? 32 : (Nn <= 64 ? 64 : 128);
+  const int tiles = ((Mm + tc::kM - 1) / tc::kM) * ((Nn + BN - 1) / BN);
+  const int nsm = std::max(device_sm_count(), 1);
+  int splits = 1;
+  if (split_k && tiles < nsm) splits = std::max(1, std::min((2 * nsm) / tiles, (K + tc::kKC - 1) / tc::kKC));
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + tc::kKC - 1) / tc::kKC * tc::kKC;
+  splits = (K + kchunk - 1) / kchunk;
+  if (splits > 1) {
+    cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * ldc * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((Nn + BN - 1) / BN, (Mm + tc::kM - 1) / tc::kM, splits);
+  if (BN == 32) return launch_tc<32>(grid, Ap, asm_, ask, Bp, bsk, bsn, C, scm, scn, Mm, Nn, K, kchunk, st);
+  if (BN == 64) return launch_tc<64>(grid, Ap, asm_, ask, Bp, bsk, bsn, C, scm, scn, Mm, Nn, K, kchunk, st);
+  return launch_tc<128>(grid, Ap, asm_, ask, Bp, bsk, bsn, C, scm, scn, Mm, Nn, K, kchunk, st);
+}
 
 cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, long sbk, long sbn, float* C, int ldc,
                         int M, int N, int K, cudaStream_t st, bool split_k);
@@ -550,6 +628,8 @@ cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, lon
     count_launches(1);
     return cudaGetLastError();
   }
+  if (g_gemm_engine == ATKM_GEMM_TCGEN05 && g_tc_err)
+    return gemm_tc(A, sam, sak, Bm, sbk, sbn, C, ldc, M, N, K, st, split_k);
   int splits = 1;
   const int tiles = ((M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
   const int nsm = std::max(device_sm_count(), 1);
@@ -645,6 +725,8 @@ int atkm_guess_net_create(atkm_guess_net** out, unsigned long long seed, void* s
   cudaError_t e = cudaSuccess;
   for (float** p : {&n->w, &n->g, &n->m, &n->v})
     if (e == cudaSuccess) e = cudaMalloc((void**)p, kL.total * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->tc_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->tc_err, 0, sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->w, 0, kL.total * sizeof(float), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, kL.total * sizeof(float), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, kL.total * sizeof(float), st);
@@ -675,6 +757,7 @@ void atkm_guess_net_destroy(atkm_guess_net* n) {
   net_free_acts(n);
   for (float* p : {n->w, n->g, n->m, n->v})
     if (p) cudaFree(p);
+  if (n->tc_err) cudaFree(n->tc_err);
   delete n;
 }
 
@@ -693,6 +776,7 @@ int atkm_guess_net_set_params(atkm_guess_net* n, const float* src, void* stream)
 int atkm_guess_net_forward(atkm_guess_net* n, int batch, const float* feats, double* psi, void* stream) {
   if (!n || !feats || !psi || batch < 1) return net_fail(n, ATKM_ERR_ARG, "atkm_guess_net_forward: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  EngineScope scope(n);
   cudaError_t e = net_ensure(n, batch);
   if (e == cudaSuccess) {
     k_pad_features<<<ew_grid((long)batch * kFpad), 256, 0, st>>>(feats, n->fpad, batch);
@@ -711,6 +795,7 @@ int atkm_guess_net_grad(atkm_guess_net* n, int batch, const float* feats, const 
                         float* loss, void* stream) {
   if (!n || !feats || !targets || !loss || batch < 1) return net_fail(n, ATKM_ERR_ARG, "atkm_guess_net_grad: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
+  EngineScope scope(n);
   cudaError_t e = net_ensure(n, batch);
   if (e == cudaSuccess) {
     k_pad_features<<<ew_grid((long)batch * kFpad), 256, 0, st>>>(feats, n->fpad, batch);
@@ -735,6 +820,27 @@ int atkm_guess_net_train_step(atkm_guess_net* n, int batch, const float* feats, 
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ATKM_OK : cuda_fail(nullptr, e, "atkm_guess_net_train_step");
+}
+
+int atkm_guess_net_set_gemm_engine(atkm_guess_net* n, int engine) {
+  if (!n || (engine != ATKM_GEMM_TCGEN05 && engine != ATKM_GEMM_MMA_SYNC))
+    return fail(nullptr, ATKM_ERR_ARG, "atkm_guess_net_set_gemm_engine: bad argument");
+  n->gemm_engine = engine;
+  return ATKM_OK;
+}
+
+int atkm_guess_net_check(atkm_guess_net* n, void* stream) {
+  if (!n) return fail(nullptr, ATKM_ERR_ARG, "atkm_guess_net_check: net is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, n->tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "atkm_guess_net_check");
+  if (flag) {
+    cudaMemsetAsync(n->tc_err, 0, sizeof(unsigned), st);
+    return fail(nullptr, ATKM_ERR_TIMEOUT, "atkm_guess_net_check: a tensor-core GEMM gave up waiting for its MMAs");
+  }
+  return ATKM_OK;
 }
 
 /* One training step (as atkm_guess_net_train_step) with its GEMMs timed by

@@ -30,6 +30,65 @@ def _timed(fn):
     return out, time.perf_counter() - t0
 
 
+def _summary(res, seconds):
+    st = collections.Counter(r["status_name"] for r in res)
+    return dict(seconds=seconds, statuses=dict(st), iters=[r["iters"] for r in res],
+                residual=[r["residual"] for r in res], E=[r["E"] for r in res],
+                device_loop=all(r.get("device_loop", False) for r in res))
+
+
+def _agreement(res, ref):
+    both = [(a, b) for a, b in zip(res, ref) if a["status"] == B.ATKM_OK and b["status"] == B.ATKM_OK]
+    dE = [(a["E"] - b["E"]) / abs(b["E"]) for a, b in both]
+    return dict(both_converged=len(both), same_energy=sum(abs(d) <= 1e-9 for d in dE),
+                lower_energy=sum(d < -1e-9 for d in dE), higher_energy=sum(d > 1e-9 for d in dE),
+                max_abs_rel_dE_same=max([abs(d) for d in dE if abs(d) <= 1e-9], default=0.0))
+
+
+def to_tolerance(problems, psi0_fn, max_iter=12000, tol=1e-8, log=print, autotune=True):
+    """The sweep to the residual tolerance three ways on the same autotuned
+    plans: every instance alone in binary64, one after another (the plain
+    method); all instances in one graph launch in binary64 (the batching
+    alone: the same arithmetic, so the same trajectories and energies); and
+    all in one launch in the double-word split form (FP32 bulk phase)."""
+    plans = [B.Plan(p.N, p.L, p.n, f32=True, df32=True, autotune=autotune) for p in problems]
+    prms = [B.make_params(p.gamma, p.beta, p.lam, p.Omega) for p in problems]
+
+    def psis():
+        return [torch.from_numpy(psi0_fn(p)).cuda() for p in problems]
+
+    out = dict(instances=len(problems), grids=[list(p.N) for p in problems], tol=tol, max_iter=max_iter,
+               autotune=autotune)
+    if autotune:
+        tun = [t for pl in plans for t in pl.tuning()]
+        out["tuning"] = dict(entries=len(tun), changed=sum(1 for t in tun if t["ms_best"] < t["ms_default"]),
+                             mixed_radix=sum(1 for t in tun if t["engine"] == 1),
+                             narrowed_tiles=sum(1 for t in tun if t["engine"] == 2 and t["tile_shift"] > 0),
+                             ms_default=sum(t["ms_default"] for t in tun), ms_best=sum(t["ms_best"] for t in tun))
+    try:
+        for prec in (B.PRECISION_F64, B.PRECISION_DF32_SPLIT):  # capture every instance's graphs once
+            B.pcg_ground_state_batched(plans, prms, psis(), max_iter=3, precision=prec)
+        ps = psis()
+        ref, tr = _timed(lambda: [pl.pcg_ground_state(pr, p, max_iter=max_iter, tol_residual=tol,
+                                                      precision=B.PRECISION_F64)
+                                  for pl, pr, p in zip(plans, prms, ps)])
+        out["f64_one_by_one"] = _summary(ref, tr)
+        log(f"binary64, one by one: {tr:.1f} s, {out['f64_one_by_one']['statuses']}")
+        for name, prec in (("f64_batched", B.PRECISION_F64), ("df32_split_batched", B.PRECISION_DF32_SPLIT)):
+            ps = psis()
+            res, t = _timed(lambda: B.pcg_ground_state_batched(plans, prms, ps, max_iter=max_iter, tol_residual=tol,
+                                                               precision=prec))
+            out[name] = _summary(res, t)
+            out[name]["speedup_vs_f64_one_by_one"] = tr / t
+            out[name]["energy_vs_f64_one_by_one"] = _agreement(res, ref)
+            log(f"{name}: {t:.1f} s ({tr / t:.2f}x), {out[name]['statuses']}, "
+                f"energies {out[name]['energy_vs_f64_one_by_one']}")
+    finally:
+        for pl in plans:
+            pl.close()
+    return out
+
+
 def run(problems, psi0_fn, iters=40, full_iters=3000, tol=1e-8, precisions=(B.PRECISION_F32_F64, B.PRECISION_F64),
         log=print, reference=False, autotune=True):
     torch.cuda.synchronize()

@@ -61,9 +61,14 @@ def _targets(B, seed):
     return rng.standard_normal((B,) + GN.OUT) + 1j * rng.standard_normal((B,) + GN.OUT)
 
 
-@pytest.mark.parametrize("B", [1, 3])
-def test_forward_matches_oracle(lib, B):
+ENGINES = {"tcgen05": 0, "mma_sync": 1}
+
+
+@pytest.mark.parametrize("engine", list(ENGINES))
+@pytest.mark.parametrize("B", [1, 3, 33])
+def test_forward_matches_oracle(lib, B, engine):
     net = lib.GuessNet(seed=1)
+    net.set_gemm_engine(ENGINES[engine])
     p = _params(20 + B)
     net.set_params(dev(p))
     f = _feats(B, 30 + B)
@@ -71,11 +76,14 @@ def test_forward_matches_oracle(lib, B):
     ref = GN.out_to_psi(GN.forward(p, f, bf16=True)["o"], B)
     assert got.shape == ref.shape
     assert rel2(got, ref) <= 2e-3
+    net.check()
 
 
-@pytest.mark.parametrize("B", [2, 5])
-def test_gradient_matches_oracle(lib, B):
+@pytest.mark.parametrize("engine", list(ENGINES))
+@pytest.mark.parametrize("B", [2, 5, 32])
+def test_gradient_matches_oracle(lib, B, engine):
     net = lib.GuessNet(seed=2)
+    net.set_gemm_engine(ENGINES[engine])
     p = _params(40 + B)
     net.set_params(dev(p))
     f, t = _feats(B, 50 + B), _targets(B, 60 + B)
@@ -90,6 +98,40 @@ def test_gradient_matches_oracle(lib, B):
         errs[name] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
     tol = {name: (1e-2 if name in ("W1", "b1") else 5e-3) for name, _ in GN.SHAPES}
     assert all(errs[k] <= tol[k] for k in errs), errs
+    net.check()
+
+
+def test_tcgen05_and_mma_sync_engines_agree(lib):
+    """The two engines round the same operands to BF16 and sum in FP32, so
+    they differ only by summation order (and the rare BF16 rounding of a
+    staged activation that it flips): forward outputs and every gradient
+    block agree well inside the oracle bars, at the training batch (32) and at
+    a ragged one (37), and the tensor-core waits all completed."""
+    p = _params(77)
+    for B in (32, 37):
+        f, t = _feats(B, 78 + B), _targets(B, 79 + B)
+        outs = {}
+        for name, eng in ENGINES.items():
+            net = lib.GuessNet(seed=5)
+            net.set_gemm_engine(eng)
+            net.set_params(dev(p))
+            psi = host(net.forward(dev(f)))
+            g, loss = net.grad(dev(f), dev(t))
+            net.check()
+            outs[name] = (psi, host(g).astype(np.float64), float(host(loss)[0]))
+        a, b = outs["tcgen05"], outs["mma_sync"]
+        assert rel2(a[0], b[0]) <= 5e-4
+        assert abs(a[2] - b[2]) <= 1e-4 * abs(b[2])
+        offs = np.cumsum([0] + [int(np.prod(s)) for _, s in GN.SHAPES])
+        for k, (name, _) in enumerate(GN.SHAPES):
+            x, y = a[1][offs[k]:offs[k + 1]], b[1][offs[k]:offs[k + 1]]
+            assert np.linalg.norm(x - y) <= 2e-3 * max(np.linalg.norm(y), 1e-30), name
+
+
+def test_gemm_engine_rejects_unknown_value(lib):
+    net = lib.GuessNet(seed=6)
+    with pytest.raises(lib.AtkmError):
+        net.set_gemm_engine(7)
 
 
 def test_init_and_param_roundtrip(lib):
