@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true", help="skip the FP32-bulk arm")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the multigrid solves to 1e-8")
-    ap.add_argument("--ttt", default="f64,f32_f64,df32_split,df32_split_all",
+    ap.add_argument("--ttt", default="f64,f32_f64,f32_split,df32_split,df32_split_all",
                     help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split; "
                          "a form runs on the finest level, or on every level with the suffix _all)")
     ap.add_argument("--case", choices=["step", "sweep"], default="step",
@@ -620,8 +620,8 @@ def timing_case(case: str):
 def study_case(case: str):
     """iterations: Algorithm 1 (binary64, one level, guess (d), residual 1e-8)
     on Example 3.1 (Cases I and II, Omega = 0.2 and 0.6) at 32^3 ... 256^3,
-    on the 32x32x16 workload and on the bench box at 64x64x16 and
-    128x128x32: iterations and the step-control events per run.
+    on the 32x32x16 and 128x128x32 workloads and on the bench box at
+    64x64x16 and 128x128x32: iterations and the step-control events per run.
     virial_vs_tol: Example 3.1 Case II, Omega = 0.8 by Algorithm 2 (32^3,
     64^3, 128^3 in binary64 from guess (a)), then the 128^3 solve continued
     to residual 1e-9 ... 1e-12: |I| and the energy terms at each."""
@@ -658,6 +658,8 @@ def study_case(case: str):
                            W.guess_phi_d(N, L, gamma, Om))
         w1 = W.CONFIGS["cfg1_32x32x16"]
         single(w1.name, w1.N, w1.L, w1.gamma, w1.beta, w1.lam, w1.n, w1.Omega, W.initial_guess(w1))
+        w2 = W.CONFIGS["cfg2_128x128x32"]
+        single(w2.name, w2.N, w2.L, w2.gamma, w2.beta, w2.lam, w2.n, w2.Omega, W.initial_guess(w2))
         w3 = W.CONFIGS[WORKLOAD]
         for N in ((64, 64, 16), (128, 128, 32)):
             single(w3.name + "_box", N, w3.L, w3.gamma, w3.beta, w3.lam, w3.n, w3.Omega,
