@@ -26,9 +26,10 @@ template <typename R> using cx = typename CT<R>::c;
 template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
   cx<R> z; z.x = a; z.y = b; return z;
 }
-// binary64 <-> binary32 conversions for the FP32 passes done on the integer
-// pipe from the IEEE-754 bit layouts (the hardware conversion instructions
-// share the slow FP64 pipe on this part).  binary64 -> binary32 rounds the 29
+// binary64 <-> binary32 conversions on the integer pipe from the IEEE-754 bit
+// layouts (the hardware conversion instructions share the slow FP64 pipe on
+// this part; each FP32 pass uses these, the hardware or a mix, whichever was
+// measured faster for it: see from64 in ops.cuh).  binary64 -> binary32 rounds the 29
 // dropped mantissa bits half-up (a mantissa carry moves into the exponent),
 // flushes results below the binary32 normal range to signed zero and
 // saturates to infinity (a NaN becomes an infinity); binary32 -> binary64 is

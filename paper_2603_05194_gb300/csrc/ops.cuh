@@ -66,7 +66,36 @@ template <typename R> inline PhysR<R> make_physr(const Phys& p) {
 __device__ __forceinline__ int kfreq(int m, int M) { return m < (M >> 1) ? m : m - M; }
 __device__ __forceinline__ int iabs(int a) { return a < 0 ? -a : a; }
 
-template <typename R> __device__ __forceinline__ cx<R> from64(double2 z) { return mk<R>(tor<R>(z.x), tor<R>(z.y)); }
+// binary64 <-> binary32 at a pass's FP64 interfaces, three ways: on the
+// integer pipe (d2f_bits / f2d_bits), with the hardware conversion (it issues
+// on the FP64 pipe), or mixed: the real part in hardware, the imaginary part
+// on the integer pipe.  The hardware instruction is the shorter dependency
+// chain, the integer routine leaves the FP64 pipe free; which wins depends on
+// how many conversions a pass makes per element, and each op below uses the
+// way measured fastest for it at 256x256x64 (FP32 H x pass 40.7 -> 30.7 us
+// mixed, H y 45.5 -> 38.8 us in hardware, H z 65.1 -> 63.2 us mixed; the
+// ATKM x forward pass, four conversions an element, stays on the integer
+// pipe).  Both round to nearest for finite values (ties away from zero on the
+// integer pipe, to even in hardware).
+enum CvtMode { kCvtInt = 0, kCvtMixed = 1, kCvtHw = 2 };
+template <typename R, int CV = kCvtInt> __device__ __forceinline__ cx<R> from64(double2 z) {
+  if constexpr (std::is_same<R, float>::value && CV == kCvtHw) {
+    return mk<R>(__double2float_rn(z.x), __double2float_rn(z.y));
+  } else if constexpr (std::is_same<R, float>::value && CV == kCvtMixed) {
+    return mk<R>(__double2float_rn(z.x), d2f_bits(z.y));
+  } else {
+    return mk<R>(tor<R>(z.x), tor<R>(z.y));
+  }
+}
+template <typename R, int CV = kCvtInt> __device__ __forceinline__ double2 to64(R a, R b) {
+  if constexpr (std::is_same<R, float>::value && CV == kCvtHw) {
+    return make_double2((double)a, (double)b);
+  } else if constexpr (std::is_same<R, float>::value && CV == kCvtMixed) {
+    return make_double2((double)a, f2d_bits(b));
+  } else {
+    return make_double2(tod<R>(a), tod<R>(b));
+  }
+}
 
 // Loads of a pass's read-only inputs through the non-coherent path, so that
 // the compiler may issue them ahead of the thread's earlier stores (a pass's
@@ -765,7 +794,7 @@ template <typename R> struct OpAtkmXI : OpBase<1, false, 0, true> {
   __device__ void store(int o, int, int m, cx<R> v, R*) const {
     if (2 * m < c.Nx) {
       double2* dst = reinterpret_cast<double2*>(phi + (size_t)o * c.Nx + 2 * m);
-      *dst = make_double2(tod<R>(v.x), tod<R>(v.y));
+      *dst = to64<R, kCvtMixed>(v.x, v.y);
     }
   }
 };
@@ -775,7 +804,7 @@ template <typename R> struct OpAtkmXI : OpBase<1, false, 0, true> {
 template <typename R, bool RED> struct OpHX : OpBase<-1, true, RED ? 2 : 0, true> {
   const double2* f; cx<R>* acc; Cst<R> c; R Omega; AxT ax, ay;
   __device__ bool valid(int o, int) const { return o < c.Nz * c.Ny; }
-  __device__ cx<R> load(int o, int, int pos) const { return from64<R>(f[(size_t)o * c.Nx + pos]); }
+  __device__ cx<R> load(int o, int, int pos) const { return from64<R, kCvtMixed>(f[(size_t)o * c.Nx + pos]); }
   __device__ void spectral(int o, int, int k, cx<R>& v, R* a) const {
     if constexpr (std::is_same<R, double>::value) {
       const double kin = ax.kinN[k], rot = Omega * ay.xc[o % c.Ny] * ax.nuN[k];
@@ -805,7 +834,7 @@ template <typename R, bool RED> struct OpHX : OpBase<-1, true, RED ? 2 : 0, true
 template <typename R, bool RED> struct OpHY : OpBase<-1, true, RED ? 2 : 0, false> {
   const double2* f; cx<R>* acc; Cst<R> c; R Omega; AxT ax, ay;
   __device__ bool valid(int, int x) const { return x < c.Nx; }
-  __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)o * c.Ny + pos) * c.Nx + x]); }
+  __device__ cx<R> load(int o, int x, int pos) const { return from64<R, kCvtHw>(f[((size_t)o * c.Ny + pos) * c.Nx + x]); }
   __device__ void spectral(int, int x, int k, cx<R>& v, R* a) const {
     if constexpr (std::is_same<R, double>::value) {
       const double kin = ay.kinN[k], rot = -Omega * ax.xc[x] * ay.nuN[k];
@@ -850,7 +879,7 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   AxT ax, ay, az;
   bool same = false;  // f == phi (H phi): phi is not read a second time
   __device__ bool valid(int, int x) const { return x < c.Nx; }
-  __device__ cx<R> load(int o, int x, int pos) const { return from64<R>(f[((size_t)pos * c.Ny + o) * c.Nx + x]); }
+  __device__ cx<R> load(int o, int x, int pos) const { return from64<R, kCvtMixed>(f[((size_t)pos * c.Ny + o) * c.Nx + x]); }
   __device__ void spectral(int, int, int k, cx<R>& v, R* a) const {
     if constexpr (std::is_same<R, double>::value) {
       const double m = az.kinN[k];
@@ -866,7 +895,7 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   }
   __device__ void store(int o, int x, int pos, cx<R> v, R* a) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
-    finish(o, x, pos, idx, v, a, tor<R>(ldro(Phi + idx)), ldro(acc + idx), from64<R>(ldro(f + idx)));
+    finish(o, x, pos, idx, v, a, tor<R>(ldro(Phi + idx)), ldro(acc + idx), from64<R, kCvtMixed>(ldro(f + idx)));
   }
   // FP32 and double-word: f at this point is the element the engine loaded
   // (the same conversion of the same value), kept in registers
@@ -885,7 +914,7 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
   __device__ void store_pre(int o, int x, int pos, cx<R> v, R* a, const unsigned char* src) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
     finish(o, x, pos, idx, v, a, tor<R>(*reinterpret_cast<const double*>(src)),
-           *reinterpret_cast<const cx<R>*>(src + 8), from64<R>(ldro(f + idx)));
+           *reinterpret_cast<const cx<R>*>(src + 8), from64<R, kCvtMixed>(ldro(f + idx)));
   }
   __device__ void store_pre_k(int o, int x, int pos, cx<R> v, R* a, const unsigned char* src, cx<R> fin) const {
     const size_t idx = ((size_t)pos * c.Ny + o) * c.Nx + x;
@@ -901,11 +930,11 @@ template <typename R, bool RED> struct OpHZ : OpBase<-1, true, RED ? 6 : 0, fals
       const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)o * c.hy, zc = -c.Lz + (R)pos * c.hz;
       V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
     }
-    const cx<R> pv = same ? fv : from64<R>(ldro(phi + idx));
+    const cx<R> pv = same ? fv : from64<R, kCvtMixed>(ldro(phi + idx));
     const R w = V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + ph.lambda * Pd;
     const cx<R> kin = add<R>(accv, v);
     const R ox = kin.x + w * fv.x, oy = kin.y + w * fv.y;
-    Hf[idx] = make_double2(tod<R>(ox), tod<R>(oy));
+    Hf[idx] = to64<R, kCvtMixed>(ox, oy);
     if (RED) {
       const R f2 = fv.x * fv.x + fv.y * fv.y;
       a[1] += V * f2;
@@ -923,7 +952,7 @@ __device__ __forceinline__ R pv_rsqrt(const Cst<R>& c, const PhysR<R>& ph, R alp
                                       double Pd64) {
   const R xc = -c.Lx + (R)x * c.hx, yc = -c.Ly + (R)y * c.hy, zc = -c.Lz + (R)z * c.hz;
   const R V = (R)0.5 * (ph.gx2 * xc * xc + ph.gy2 * yc * yc + ph.gz2 * zc * zc);
-  const cx<R> pv = from64<R>(p64);
+  const cx<R> pv = from64<R, kCvtMixed>(p64);
   const R Pd = tor<R>(Pd64);
   const R den = alpha + V + ph.beta * (pv.x * pv.x + pv.y * pv.y) + fabs(ph.lambda) * (Pd > (R)0 ? Pd : (R)0);
   return rsq<R>(den);
@@ -948,7 +977,7 @@ template <typename R> struct OpPXF : OpBase<-1, false, 0, true> {
       return scl<R>(r[idx], w);
     }
     const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, phi[idx], Phi[idx]);
-    return scl<R>(from64<R>(r[idx]), w);
+    return scl<R>(from64<R, kCvtMixed>(r[idx]), w);
   }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
   __device__ void store(int o, int, int pos, cx<R> v, R*) const { Wk[(size_t)o * c.Nx + pos] = v; }
@@ -994,7 +1023,7 @@ template <typename R> struct OpPXI : OpBase<1, false, 0, true> {
       return;
     }
     const R w = pv_rsqrt<R>(c, ph, tor<R>(*alpha), pos, o % c.Ny, o / c.Ny, ldro(phi + idx), ldro(Phi + idx));
-    Pr[idx] = make_double2(tod<R>(w * v.x), tod<R>(w * v.y));
+    Pr[idx] = to64<R, kCvtMixed>(w * v.x, w * v.y);
   }
 };
 
