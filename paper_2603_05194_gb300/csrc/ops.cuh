@@ -674,7 +674,8 @@ inline cudaError_t run_pass(const Op& op, const FftLen& f, const PassGrid& pg, c
 // and z passes then run on the Nx + 1 half-spectrum columns only, and the
 // inverse x transform rebuilds the real output from that half (C2R).  With a
 // real density this equals the real part of the full complex convolution
-// once K is symmetrised on the padded Nyquist planes (see OpAtkmZ).
+// once K is symmetrised on the padded Nyquist planes (see OpAtkmZ).  W1 and
+// W2 hold 2 X (the post-twist's 1/2 sits in the z pass's multiplier).
 // W1: [Nz][Ny][XS], W2: [Nz][My][XS], columns 0..Nx used.
 template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
   static constexpr bool kMirror = true;
@@ -697,14 +698,20 @@ template <typename R, int MODE> struct OpAtkmXF : OpBase<-1, false, 0, true> {
     const size_t idx = (size_t)o * c.Nx + 2 * m;
     return mk<R>(dens(idx), dens(idx + 1));
   }
+  // Stores 2 X_k: the factor 1/2 of E and D is left to the z pass's
+  // multiplier, where it costs nothing (a power of two commutes exactly with
+  // every later sum and product, so the result is the same to the bit).
   __device__ void post(int o, int, int k, cx<R> Zk, cx<R> Zm, R*) const {
     const cx<R> Zc = mk<R>(Zm.x, -Zm.y);                 // conj Z_{Nx-k}
-    const cx<R> E = scl<R>(add<R>(Zk, Zc), (R)0.5);
-    const cx<R> D = scl<R>(sub<R>(Zk, Zc), (R)0.5);
+    const cx<R> E2 = add<R>(Zk, Zc);                      // 2 E
+    const cx<R> D2 = sub<R>(Zk, Zc);                      // 2 D
     const cx<R> w = twM[k];                               // e^{-2 pi i k / Mx}
-    const cx<R> wD = cmul<R>(w, D);
-    W1[(size_t)o * XS + k] = mk<R>(E.x + wD.y, E.y - wD.x);  // E - i w D
-    if (k == 0) W1[(size_t)o * XS + c.Nx] = mk<R>(Zk.x - Zk.y, (R)0);
+    const cx<R> wD = cmul<R>(w, D2);
+    W1[(size_t)o * XS + k] = mk<R>(E2.x + wD.y, E2.y - wD.x);  // 2 (E - i w D)
+    if (k == 0) {
+      const R xn = Zk.x - Zk.y;
+      W1[(size_t)o * XS + c.Nx] = mk<R>(xn + xn, (R)0);
+    }
   }
   __device__ void spectral(int, int, int, cx<R>&, R*) const {}
   __device__ void store(int, int, int, cx<R>, R*) const {}
@@ -723,7 +730,8 @@ template <typename R> struct OpAtkmYF : OpBase<-1, false, 0, false> {
   __device__ void store(int o, int x, int pos, cx<R> v, R*) const { W2[((size_t)o * c.My + pos) * XS + x] = v; }
 };
 
-// z forward * K_sym / (Mx My Mz) * inverse: o = ky, x = kx in [0, Nx]; rows z < Nz.
+// z forward * K_sym / (2 Mx My Mz) * inverse: o = ky, x = kx in [0, Nx]; rows z < Nz
+// (the 2 undoes the doubled half spectrum that OpAtkmXF stores).
 // K_sym = (K(k) + K(-k))/2 = -1 + 3 U0 (A^2 + B^2), A = sum of n_a nu_a over
 // axes whose index is not the padded Nyquist index, B over those that are.
 // FP64 and double-word passes are bound by arithmetic: they read K_sym, pre-

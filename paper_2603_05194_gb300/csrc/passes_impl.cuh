@@ -133,7 +133,7 @@ cudaError_t atkm_pass_z(atkm_plan* p, int, const double*, const double*, double*
   if (!x.W2 || !x.K) return cudaErrorInvalidValue;
   OpAtkmZ<R> op; op.W2 = x.W2; op.K = x.K; op.U0 = x.K; op.c = x.c; op.XS = g.XS;
   op.n0 = (R)p->n[0]; op.n1 = (R)p->n[1]; op.n2 = (R)p->n[2];
-  op.invM = (R)(1.0 / ((double)g.Mx * g.My * g.Mz));
+  op.invM = (R)(0.5 / ((double)g.Mx * g.My * g.Mz));  // with the x forward pass's 1/2 (OpAtkmXF)
   const PassGrid pg = pass_grid<R>(p, g.Mz, false, 0, g.Xh, g.My);
   ATKM_RUN(nm<R>("atkm_z_f64", "atkm_z_f32", "atkm_z_df"), 4 * x.H1 * x.s + x.kb, x.fz, op, p->fM[2], pg);
   return cudaSuccess;

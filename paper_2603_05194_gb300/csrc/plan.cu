@@ -203,7 +203,8 @@ __global__ void k_multiplier_full(double* __restrict__ K, const double* __restri
 }
 
 // The multiplier of the z pass on the Nx + 1 half-spectrum columns, with the
-// inverse transform's 1 / (Mx My Mz) folded in.  A real density's spectrum is
+// inverse transform's 1 / (Mx My Mz) and the factor 1/2 of the x forward
+// pass's post-twist (OpAtkmXF) folded in.  A real density's spectrum is
 // Hermitian, so the real-data ATKM uses the symmetrised multiplier
 // K_sym(k) = (K(k) + K(-k)) / 2 = -1 + 3 U0(nu_k) (A^2 + B^2), where A sums
 // n_a nu_a over the axes whose index is not the padded Nyquist index M_a / 2
@@ -215,7 +216,7 @@ __global__ void k_multiplier_half(double* __restrict__ Kh, const double* __restr
                                   double n1, double n2) {
   const size_t total = (size_t)g.Mz * g.My * g.XS;
   const double px = kPi / (2.0 * g.Lx), py = kPi / (2.0 * g.Ly), pz = kPi / (2.0 * g.Lz);
-  const double invM = 1.0 / ((double)g.Mx * g.My * g.Mz);
+  const double invM = 0.5 / ((double)g.Mx * g.My * g.Mz);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.XS);
     const int o = (int)((i / g.XS) % g.My);
