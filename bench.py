@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
                                                "profiling_overhead", "polish_df32", "fp64_peak", "iterations",
                                                "virial_vs_tol", "engines", "finest_level", "basin",
-                                               "f32_floor", "mg_policy", "guess_gemm"],
+                                               "f32_floor", "mg_policy", "guess_gemm", "autotune"],
                     help="run a small fixed amount of work on the bench grid for an ncu capture, or one of the "
                          "timings quoted in the design notes, and exit")
     a = ap.parse_args()
@@ -685,6 +685,42 @@ def study_case(case: str):
         p.close()
 
 
+def autotune_case():
+    """autotune: the FFT-tile autotuner on the 48 plans of the uneven-grid
+    sweep (FP32, binary64 and double-word arithmetic): every tuned (length,
+    layout, arithmetic) entry with the engine and tile it picked and the
+    default's and the winner's time on the plan's own ATKM + H + P, then a
+    summary line."""
+    import collections
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+    B.load_library()
+    names = {0: "f64", 1: "f32", 2: "df32"}
+    rows = {}
+    t0 = time.perf_counter()
+    for p in W.sweep_instances(48):
+        plan = B.Plan(p.N, p.L, p.n, f32=True, df32=True, autotune=True)
+        for t in plan.tuning():
+            key = (names[t["precision"]], t["length"], "x" if t["line_major"] else "yz")
+            pick = "mixed-radix" if t["engine"] == 1 else f"generic/{1 << t['tile_shift']}"
+            rows.setdefault(key, collections.Counter())[pick] += 1
+            rows[key]["_ms_default"] += t["ms_default"]
+            rows[key]["_ms_best"] += t["ms_best"]
+            rows[key]["_n"] += 1
+        plan.close()
+    secs = time.perf_counter() - t0
+    for (prec, L, lay), c in sorted(rows.items()):
+        picks = {k: v for k, v in c.items() if not k.startswith("_")}
+        print(json.dumps({"case": "autotune", "arith": prec, "length": L, "layout": lay, "plans": c["_n"],
+                          "picks": picks, "ms_default_sum": round(c["_ms_default"], 3),
+                          "ms_best_sum": round(c["_ms_best"], 3)}), flush=True)
+    tot_d = sum(c["_ms_default"] for c in rows.values())
+    tot_b = sum(c["_ms_best"] for c in rows.values())
+    print(json.dumps({"case": "autotune", "summary": True, "plans": 48, "seconds_with_plan_creation": round(secs, 1),
+                      "entries": sum(c["_n"] for c in rows.values()), "ms_default_sum": round(tot_d, 3),
+                      "ms_best_sum": round(tot_b, 3)}), flush=True)
+
+
 def guess_gemm_case():
     """guess_gemm: one training step of the learned-guess network at batch 32
     (seeded random features and targets), its GEMMs bracketed by CUDA events,
@@ -921,6 +957,9 @@ def profile_case(case: str):
         return
     if case == "guess_gemm":
         guess_gemm_case()
+        return
+    if case == "autotune":
+        autotune_case()
         return
     if case == "fp64_peak":
         from paper_2603_05194_gb300 import binding as B
