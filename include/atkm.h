@@ -130,8 +130,9 @@ int atkm_measure_fp64_fma(int blocks_per_sm, int iters, int repeats, double* gfl
  * plan's passes that is not a power of two, per arithmetic the plan carries
  * (binary64; FP32 with ATKM_PLAN_F32; double-word with ATKM_PLAN_DF32) and per
  * layout (line-major x pass, strided y / z pass), times the candidates -- the
- * mixed-radix register engine (lengths 3 * 2^a, 5 * 2^a <= 384; not double-
- * word; not with ATKM_PLAN_GENERIC_FFT) and the generic shared-memory engine
+ * mixed-radix register engine (FP32: lengths 3 * 2^a and 5 * 2^a <= 384;
+ * binary64: 3 * 2^a <= 384; not double-word; not with ATKM_PLAN_GENERIC_FFT)
+ * and the generic shared-memory engine
  * at its default tile width, 1/2 and 1/4 of it -- on the plan's own ATKM of
  * |psi|^2, H psi and P r (CUDA events on `stream`, best of 3 after a warm-up)
  * and keeps the fastest; every later pass of that length and layout uses it.
