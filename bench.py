@@ -65,9 +65,10 @@ def parse():
     ap.add_argument("--ttt", default="f64,f32_f64,f32_split,df32_split,df32_split_all",
                     help="precision forms timed to residual 1e-8 (comma list of f64, f32_f64, f32_split, df32_split; "
                          "a form runs on the finest level, or on every level with the suffix _all)")
-    ap.add_argument("--case", choices=["step", "sweep"], default="step",
+    ap.add_argument("--case", choices=["step", "sweep", "guess"], default="step",
                     help="step: the PCG step on 256x256x64 (default); sweep: the 48-instance uneven-grid sweep to "
-                         "residual 1e-8 (batched vs one by one), one JSON line")
+                         "residual 1e-8 (batched vs one by one); guess: the learned initial guess against guess (d), "
+                         "binary64 PCG to residual 1e-8 at 128x128x32; one JSON line each")
     ap.add_argument("--sweep-max-iter", type=int, default=12000, help="iteration cap of each sweep instance")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["atkm_f32", "atkm_f64", "atkm_df32", "pcg_f64", "pcg_mixed",
@@ -1020,6 +1021,65 @@ def sweep_line(args):
     print(json.dumps(line))
 
 
+def guess_line(args):
+    """The learned initial guess, bounded: 320 seeded draws of the learned-
+    guess workload at slow rotation (Omega mapped into [0.30, 0.45], every
+    other parameter over its full range) solved at 64x64x16 to residual 1e-7
+    as training targets, 4000 Adam steps of the network on the GPU, then 32
+    held-out draws (another seed) solved at 128x128x32 to residual 1e-8 in
+    binary64 from the network's guess (inferred at 64x64x16, spectrally
+    interpolated) and from guess (d), each arm one batched call.  value =
+    seconds of the learned arm (inference included); beside it the plain arm,
+    iterations and the energy agreement (the plain run judges)."""
+    import dataclasses
+    import torch
+    import atkm_workloads as W
+    from paper_2603_05194_gb300 import binding as B
+    from paper_2603_05194_gb300 import guess as G
+    B.load_library()
+    torch.cuda.set_device(0)
+    quiet = lambda *a, **k: None  # noqa: E731
+
+    def slow(draws):
+        return [dataclasses.replace(p, Omega=0.30 + (p.Omega - 0.30) * (0.15 / 0.65)) for p in draws]
+
+    psi0 = lambda p: W.initial_guess(p)  # noqa: E731
+    t0 = time.perf_counter()
+    train_p = slow(W.guess_draws(320, seed=5))
+    tgt, res = G.make_targets(train_p, psi0, tol=1e-7, max_iter=3000, chunk=40, log=quiet)
+    ok = [i for i, r in enumerate(res) if r["residual"] < 1e-4]
+    idx = torch.tensor(ok, device="cuda")
+    feats = G.problem_features(train_p)[idx].contiguous()
+    targets = tgt[idx].contiguous()
+    del tgt
+    t_targets = time.perf_counter() - t0
+    net = B.GuessNet(seed=0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    G.train(net, feats, targets, steps=4000, batch=32, lr=2e-3, log=quiet)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    loss = G.loss_of(net, feats, targets)
+    net.check()
+    del targets
+    ev_p = [W.with_grid(p, W.GUESS_FINE_N) for p in slow(W.guess_draws(32, seed=6))]
+    ev = G.evaluate(net, ev_p, psi0, W.GUESS_FINE_N, TOL, 6000, chunk=32, log=quiet, precision=B.PRECISION_F64)
+    t_l = ev["inference_s"] + ev["solve_s_learned"]
+    line = {"metric": "learned-guess time to residual 1e-8 (32 held-out draws at 128x128x32, binary64 PCG)",
+            "value": round(t_l, 3), "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": round(t_l * 1e3, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f64", "data": "synthetic",
+            "config": {"workload": "learned_guess_slow_64x64x16_to_128x128x32", "train_draws": len(train_p),
+                       "train_used": len(ok), "train_steps": 4000, "eval_draws": len(ev_p), "tol": TOL,
+                       "max_iter": 6000, "precision": "f64"},
+            "train": {"targets_s": round(t_targets, 2), "train_s": round(t_train, 2), "loss": loss},
+            "plain_s": round(ev["solve_s_plain"], 3), "speedup_vs_plain": round(ev["solve_s_plain"] / t_l, 3),
+            "eval": {k: v for k, v in ev.items() if k != "rows"},
+            "rows": [{k: r[k] for k in ("Omega", "iters_learned", "iters_plain", "status_learned", "status_plain",
+                                        "dE_rel")} for r in ev["rows"]]}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.cpu_sample:
@@ -1030,6 +1090,9 @@ def main():
         return
     if args.case == "sweep":
         sweep_line(args)
+        return
+    if args.case == "guess":
+        guess_line(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

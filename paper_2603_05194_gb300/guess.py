@@ -140,22 +140,23 @@ def infer_fine(net: B.GuessNet, problems, fine_N, fine_plans=None):
     return out, time.perf_counter() - t0
 
 
-def evaluate(net: B.GuessNet, problems, psi0_fn, fine_N, tol=1e-8, max_iter=6000, e_tol=1e-9, chunk=40, log=print):
+def evaluate(net: B.GuessNet, problems, psi0_fn, fine_N, tol=1e-8, max_iter=6000, e_tol=1e-9, chunk=40, log=print,
+             precision=B.PRECISION_F32_F64):
     """Held-out comparison on fine_N: PCG from the learned guess against PCG
-    from guess (d), each arm one batched call per chunk of problems.  The plain
-    run judges the final energy: an instance whose learned run does not
-    converge, or ends above the plain energy by more than e_tol relative,
-    falls back to the plain result."""
+    from guess (d), each arm one batched call per chunk of problems, both in
+    `precision`.  The plain run judges the final energy: an instance whose
+    learned run does not converge, or ends above the plain energy by more than
+    e_tol relative, falls back to the plain result."""
     res_l, res_p, t_inf, t_l, t_p = [], [], 0.0, 0.0, 0.0
     for c0 in range(0, len(problems), chunk):
         part = problems[c0:c0 + chunk]
         plans = [B.Plan(fine_N, p.L, p.n, f32=True) for p in part]
         try:
             learned, ti = infer_fine(net, part, fine_N, fine_plans=plans)
-            rl, tl = solve_batch(part, learned, fine_N, tol, max_iter, plans=plans)
+            rl, tl = solve_batch(part, learned, fine_N, tol, max_iter, precision=precision, plans=plans)
             del learned
             plain = [torch.from_numpy(psi0_fn(p)).cuda() for p in part]
-            rp, tp = solve_batch(part, plain, fine_N, tol, max_iter, plans=plans)
+            rp, tp = solve_batch(part, plain, fine_N, tol, max_iter, precision=precision, plans=plans)
             del plain
         finally:
             for pl in plans:
