@@ -439,10 +439,15 @@ int atkm_guess_net_train_step(atkm_guess_net* net, int batch, const float* feats
 /* Engine of the network's dense GEMMs: ATKM_GEMM_TCGEN05 (default; tcgen05.mma
  * with the accumulator in tensor memory, 128-row tiles) or ATKM_GEMM_MMA_SYNC
  * (warp-level mma.sync m16n8k16, kept for comparison).  Both round the
- * operands to BF16 and sum in FP32.  ATKM_ERR_ARG for another value.
- * Implementation choice; the paper has no counterpart. */
+ * operands to BF16 and sum in FP32.  ATKM_GEMM_TCGEN05_WAIT_TEST checks the
+ * tensor-core path's error reporting: every such GEMM first waits, at most
+ * 1000 polls, on a barrier that nothing completes, gives up before issuing
+ * any MMA, and leaves its output unwritten; atkm_guess_net_check then
+ * returns ATKM_ERR_TIMEOUT and the context stays usable.  ATKM_ERR_ARG for
+ * another value.  Implementation choice; the paper has no counterpart. */
 #define ATKM_GEMM_TCGEN05 0
 #define ATKM_GEMM_MMA_SYNC 1
+#define ATKM_GEMM_TCGEN05_WAIT_TEST 2
 int atkm_guess_net_set_gemm_engine(atkm_guess_net* net, int engine);
 /* Synchronises `stream` and reports whether any tcgen05 GEMM of this network
  * gave up a bounded wait for its MMAs since the last check (ATKM_ERR_TIMEOUT;

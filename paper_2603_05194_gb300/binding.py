@@ -35,6 +35,7 @@ PRECISION_F32_SPLIT = 2
 PRECISION_DF32_SPLIT = 3
 ATKM_GEMM_TCGEN05 = 0
 ATKM_GEMM_MMA_SYNC = 1
+ATKM_GEMM_TCGEN05_WAIT_TEST = 2
 
 
 class AtkmError(RuntimeError):

@@ -536,7 +536,8 @@ cudaError_t launch_tc(dim3 grid, const float* A, long sam, long sak, const float
     prepared.fetch_or(bit, std::memory_order_acq_rel);
   }
   tc::k_gemm_tc<BN><<<grid, tc::kThreads, tc::Cfg<BN>::kSmem, st>>>(A, sam, sak, Bm, sbk, sbn, C, scm, scn, M, N, K,
-                                                                      kchunk, g_tc_err);
+                                                                      kchunk, g_tc_err,
+                                                                      g_gemm_engine == ATKM_GEMM_TCGEN05_WAIT_TEST);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -628,7 +629,7 @@ cudaError_t gemm_launch(const float* A, long sam, long sak, const float* Bm, lon
     count_launches(1);
     return cudaGetLastError();
   }
-  if (g_gemm_engine == ATKM_GEMM_TCGEN05 && g_tc_err)
+  if ((g_gemm_engine == ATKM_GEMM_TCGEN05 || g_gemm_engine == ATKM_GEMM_TCGEN05_WAIT_TEST) && g_tc_err)
     return gemm_tc(A, sam, sak, Bm, sbk, sbn, C, ldc, M, N, K, st, split_k);
   int splits = 1;
   const int tiles = ((M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
@@ -823,7 +824,7 @@ int atkm_guess_net_train_step(atkm_guess_net* n, int batch, const float* feats, 
 }
 
 int atkm_guess_net_set_gemm_engine(atkm_guess_net* n, int engine) {
-  if (!n || (engine != ATKM_GEMM_TCGEN05 && engine != ATKM_GEMM_MMA_SYNC))
+  if (!n || (engine != ATKM_GEMM_TCGEN05 && engine != ATKM_GEMM_MMA_SYNC && engine != ATKM_GEMM_TCGEN05_WAIT_TEST))
     return fail(nullptr, ATKM_ERR_ARG, "atkm_guess_net_set_gemm_engine: bad argument");
   n->gemm_engine = engine;
   return ATKM_OK;

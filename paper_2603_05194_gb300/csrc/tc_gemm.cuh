@@ -20,7 +20,10 @@
 //
 // Every mbarrier wait is bounded: a wait that gives up sets *err, the CTA
 // stops issuing, waits once more (bounded) for what it already issued, frees
-// its tensor memory and leaves.
+// its tensor memory and leaves.  With wait_test set, each CTA instead waits
+// (1000 polls) on an mbarrier that nothing arrives at before issuing any MMA,
+// gives up, and takes that path: a check of the error reporting that leaves
+// no tensor-core work in flight.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -73,9 +76,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// true once the phase of the given parity has completed; false after kWaitPolls polls
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long i = 0; i < kWaitPolls; ++i) {
+// true once the phase of the given parity has completed; false after `polls` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long polls = kWaitPolls) {
+  for (long i = 0; i < polls; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -187,10 +190,11 @@ __device__ __forceinline__ void stage(unsigned char* dst, const float* __restric
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbk, long sbn,
-          float* __restrict__ C, long scm, long scn, int M, int N, int K, int kchunk, unsigned* err) {
+          float* __restrict__ C, long scm, long scn, int M, int N, int K, int kchunk, unsigned* err,
+          int wait_test) {
   using G = Cfg<BN>;
   extern __shared__ __align__(128) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ __align__(8) unsigned long long bars[3];  // [2]: the wait_test barrier
   __shared__ uint32_t tbase;
   const uint32_t raw = smem_u32(tc_smem);
   unsigned char* base = tc_smem + (((raw + 127u) & ~127u) - raw);
@@ -201,6 +205,7 @@ k_gemm_tc(const float* __restrict__ A, long sam, long sak, const float* __restri
   if (threadIdx.x == 0) {
     mbar_init(smem_u32(&bars[0]));
     mbar_init(smem_u32(&bars[1]));
+    mbar_init(smem_u32(&bars[2]));
     fence_async_smem();
   }
   fence_before();
@@ -210,7 +215,8 @@ k_gemm_tc(const float* __restrict__ A, long sam, long sak, const float* __restri
   uint32_t phase[2] = {0u, 0u};
   int it = 0;
   bool bad = false;
-  for (int k0 = kb; k0 < ke; k0 += kKC, ++it) {
+  if (wait_test) bad = __syncthreads_or(!mbar_wait(smem_u32(&bars[2]), 0u, 1000)) != 0;
+  for (int k0 = kb; k0 < ke && !bad; k0 += kKC, ++it) {
     const int s = it & 1;
     unsigned char* sA = base + s * G::kStage;
     unsigned char* sB = sA + G::kABytes;

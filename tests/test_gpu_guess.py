@@ -128,6 +128,29 @@ def test_tcgen05_and_mma_sync_engines_agree(lib):
             assert np.linalg.norm(x - y) <= 2e-3 * max(np.linalg.norm(y), 1e-30), name
 
 
+def test_tcgen05_wait_limit_reports_timeout_and_context_survives(lib):
+    """Failure path of the tensor-core GEMMs without a fault: under
+    ATKM_GEMM_TCGEN05_WAIT_TEST every tcgen05 GEMM waits (1000 polls) on a
+    barrier that nothing completes, gives up before issuing any MMA and sets
+    the network's flag; the host reads ATKM_ERR_TIMEOUT, the flag clears, and
+    the next forward pass on the same context matches the oracle."""
+    net = lib.GuessNet(seed=8)
+    p = _params(81)
+    net.set_params(dev(p))
+    f = _feats(3, 82)
+    net.set_gemm_engine(lib.ATKM_GEMM_TCGEN05_WAIT_TEST)
+    net.forward(dev(f))
+    with pytest.raises(lib.AtkmError) as ei:
+        net.check()
+    assert ei.value.code == lib.ATKM_ERR_TIMEOUT
+    net.check()  # the flag was cleared
+    net.set_gemm_engine(lib.ATKM_GEMM_TCGEN05)
+    got = host(net.forward(dev(f)))
+    ref = GN.out_to_psi(GN.forward(p, f, bf16=True)["o"], 3)
+    assert rel2(got, ref) <= 2e-3
+    net.check()
+
+
 def test_gemm_engine_rejects_unknown_value(lib):
     net = lib.GuessNet(seed=6)
     with pytest.raises(lib.AtkmError):
